@@ -1,0 +1,257 @@
+"""Seeded synthetic workloads: geometry, materials, ports and frequency lists.
+
+This module only *describes* problems (shapes, material tables, plane indices,
+seeded parameter draws).  It holds none of the solver's arithmetic and imports
+nothing from the CUDA library or from the oracle, so both sides and the tests
+can build identical inputs from it.
+
+The microstrip workloads stand in for the paper's transmission lines (Sec. II-B
+microstrip: PEC ground, dielectric substrate, strip conductor; Sec. III: layered
+oxide stack with a lossy metal line).  Propagation is along x, the strip width
+along y and the height along z; the paper's own frame propagates along y, which
+is a pure relabelling.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+# boundary kinds per face (-x, +x, -y, +y, -z, +z)
+BC_PEC = 0
+BC_PML = 1
+
+# waveform kinds
+WAVE_NONE = 0
+WAVE_DIFF_GAUSS = 1      # differential Gaussian, Eq. 3 (param0 = sigma [s])
+WAVE_GAUSS_SINE = 2      # Gaussian-modulated sine (param0 = f0 [Hz], param1 = bandwidth [Hz])
+WAVE_TABLE = 3           # user table, one value per step
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea, Flood 2014): a counter-based 64-bit generator."""
+
+    MASK = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.state = seed & self.MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & self.MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer uniform on [lo, hi] inclusive."""
+        return lo + self.next_u64() % (hi - lo + 1)
+
+
+@dataclass
+class Port:
+    plane: int            # x index of the V surface (E_z edges at x = plane)
+    direction: int        # +1: incident wave travels +x, -1: travels -x
+    j0: int               # strip edges in y (node indices), V surface j in [j0, j1]
+    j1: int
+    k0: int               # V surface z range k in [k0, k1) (E_z edges)
+    k1: int
+    kb: int               # conductor bottom / top node in z (kb == kt for a sheet)
+    kt: int
+    margin: int = 1       # I loop lies `margin` cells outside the conductor
+    width: float = 0.0    # strip width [m]; 0 -> (j1 - j0) * dy
+
+
+@dataclass
+class Source:
+    kind: int = WAVE_NONE
+    plane: int = 0
+    j0: int = 0
+    j1: int = 0
+    k0: int = 0
+    k1: int = 0
+    amplitude: float = 1.0
+    param0: float = 0.0
+    param1: float = 0.0
+    t0: float = -1.0                       # < 0: three envelope widths
+    table: Optional[np.ndarray] = None     # WAVE_TABLE samples s((n+1) dt)
+
+
+@dataclass
+class Problem:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    courant: float
+    ids: np.ndarray                        # uint8 (nz, ny, nx)
+    eps_r: np.ndarray                      # per material
+    sigma: np.ndarray
+    mu_r: np.ndarray
+    is_pec: np.ndarray                     # uint8 per material
+    sheets: List[tuple] = field(default_factory=list)   # (axis, index, lo0, hi0, lo1, hi1)
+    bc: tuple = (BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML)
+    pml_cells: int = 8
+    pml_order: int = 3
+    pml_sigma_scale: float = 1.0
+    pml_kappa_max: float = 1.0
+    pml_alpha_max: float = 0.0
+    source: Source = field(default_factory=Source)
+    ports: List[Port] = field(default_factory=list)
+    freqs: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    nsteps: int = 0
+    name: str = ""
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+def linear_freqs(f_lo: float, f_hi: float, n: int) -> np.ndarray:
+    return np.array([f_lo + k * (f_hi - f_lo) / (n - 1) for k in range(n)], dtype=np.float64)
+
+
+def microstrip(nx: int, ny: int, nz: int, delta: float, *, sub_cells: int, strip_j0: int,
+               strip_j1: int, eps_r: float, sigma: float, pml: int, bc: Sequence[int],
+               courant: float, nsteps: int, freqs: np.ndarray, f0: float, bw: float,
+               src_plane: int, port_planes: Sequence[int], uniform_cap: bool = False,
+               name: str = "") -> Problem:
+    """PEC ground at z = 0, substrate k in [0, sub_cells), zero-thickness PEC strip at
+    k = sub_cells spanning the whole length in x, air above."""
+    ids = np.zeros((nz, ny, nx), dtype=np.uint8)
+    ids[:sub_cells] = 1
+    eps = np.array([1.0, eps_r])
+    sig = np.array([0.0, sigma])
+    mu = np.array([1.0, 1.0])
+    pec = np.array([0, 0], dtype=np.uint8)
+    sheets = [(2, sub_cells, 0, nx, strip_j0, strip_j1)]
+    src = Source(kind=WAVE_GAUSS_SINE, plane=src_plane, j0=strip_j0, j1=strip_j1, k0=0,
+                 k1=sub_cells, amplitude=1.0, param0=f0, param1=bw)
+    ports = []
+    for idx, pl in enumerate(port_planes):
+        ports.append(Port(plane=pl, direction=1 if idx == 0 else -1, j0=strip_j0, j1=strip_j1,
+                          k0=0, k1=sub_cells, kb=sub_cells, kt=sub_cells, margin=1))
+    return Problem(nx=nx, ny=ny, nz=nz, dx=delta, dy=delta, dz=delta, courant=courant,
+                   ids=ids, eps_r=eps, sigma=sig, mu_r=mu, is_pec=pec, sheets=sheets,
+                   bc=tuple(bc), pml_cells=pml, source=src, ports=ports, freqs=freqs,
+                   nsteps=nsteps, name=name)
+
+
+def config_small_fp64() -> Problem:
+    """Plain FP64 microstrip: 64x32x24 cells of 5 um, eps_r 3.8 substrate of 8 cells,
+    6-cell-wide PEC sheet strip, 8-cell PML on the x ends and the top (y walls PEC),
+    Courant 0.99, 2000 steps, Gaussian-modulated sine at 300 GHz / 200 GHz bandwidth,
+    64 DFT frequencies 100-500 GHz."""
+    return microstrip(64, 32, 24, 5e-6, sub_cells=8, strip_j0=13, strip_j1=19, eps_r=3.8,
+                      sigma=0.0, pml=8, bc=(BC_PML, BC_PML, BC_PEC, BC_PEC, BC_PEC, BC_PML),
+                      courant=0.99, nsteps=2000, freqs=linear_freqs(100e9, 500e9, 64),
+                      f0=300e9, bw=200e9, src_plane=10, port_planes=(14, 50),
+                      name="microstrip 64x32x24 fp64")
+
+
+def config_lossy_line(nx: int = 768, ny: int = 384, nz: int = 256, nsteps: int = 200_000,
+                      scale_z: Optional[float] = None) -> Problem:
+    """Single large lossy line: cells of 20 nm; Si (eps_r 11.7, 10 S/m) for k < 96,
+    three SiO2 layers (eps_r 3.9) up to k = 192, a Cu strip (5.8e7 S/m) 50 cells wide and
+    10 thick, air above; 12-cell PML on +-x, +-y and +z; PEC ground; pulse 50-300 GHz;
+    128 DFT frequencies.  Smaller grids keep the same stack scaled by nz/256."""
+    s = nz / 256.0 if scale_z is None else scale_z
+    k_si, k_ox, k_cu = int(round(96 * s)), int(round(192 * s)), int(round(202 * s))
+    k_cu = max(k_cu, k_ox + 1)
+    wy = max(2, int(round(50 * ny / 384)))
+    j0 = (ny - wy) // 2
+    j1 = j0 + wy
+    ids = np.zeros((nz, ny, nx), dtype=np.uint8)
+    ids[:k_si] = 1
+    third = (k_ox - k_si) // 3
+    ids[k_si:k_si + third] = 2
+    ids[k_si + third:k_si + 2 * third] = 3
+    ids[k_si + 2 * third:k_ox] = 4
+    ids[k_ox:k_cu, j0:j1, :] = 5
+    eps = np.array([1.0, 11.7, 3.9, 3.9, 3.9, 1.0])
+    sig = np.array([0.0, 10.0, 0.0, 0.0, 0.0, 5.8e7])
+    mu = np.ones(6)
+    pec = np.zeros(6, dtype=np.uint8)
+    pml = 12
+    src_plane = pml + 2
+    src = Source(kind=WAVE_GAUSS_SINE, plane=src_plane, j0=j0, j1=j1, k0=0, k1=k_ox,
+                 amplitude=1.0, param0=175e9, param1=250e9)
+    ports = [Port(plane=src_plane + 4, direction=1, j0=j0, j1=j1, k0=0, k1=k_ox, kb=k_ox,
+                  kt=k_cu, margin=1),
+             Port(plane=nx - pml - 6, direction=-1, j0=j0, j1=j1, k0=0, k1=k_ox, kb=k_ox,
+                  kt=k_cu, margin=1)]
+    return Problem(nx=nx, ny=ny, nz=nz, dx=20e-9, dy=20e-9, dz=20e-9, courant=0.99, ids=ids,
+                   eps_r=eps, sigma=sig, mu_r=mu, is_pec=pec, sheets=[],
+                   bc=(BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML), pml_cells=pml,
+                   source=src, ports=ports, freqs=linear_freqs(50e9, 300e9, 128), nsteps=nsteps,
+                   name=f"lossy line {nx}x{ny}x{nz} 20nm")
+
+
+def batch_instance(rng: SplitMix64, nsteps: int = 20_000, nfreq: int = 64,
+                   dims: Optional[tuple] = None) -> Problem:
+    """One batched-sweep microstrip: dims 64-192 per axis, strip width 4-40 cells,
+    substrate 6-30 cells, eps_r 2-12, substrate sigma 0-50 S/m, 8-cell PML, 5 um cells."""
+    if dims is None:
+        nx, ny, nz = rng.randint(64, 192), rng.randint(64, 192), rng.randint(64, 192)
+    else:
+        nx, ny, nz = dims
+    w = rng.randint(4, 40)
+    sub = rng.randint(6, 30)
+    er = rng.uniform(2.0, 12.0)
+    sg = rng.uniform(0.0, 50.0)
+    pml = 8
+    w = min(w, ny - 2 * pml - 8)
+    sub = min(sub, nz - pml - 8)
+    j0 = (ny - w) // 2
+    return microstrip(nx, ny, nz, 5e-6, sub_cells=sub, strip_j0=j0, strip_j1=j0 + w, eps_r=er,
+                      sigma=sg, pml=pml, bc=(BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML),
+                      courant=0.99, nsteps=nsteps, freqs=linear_freqs(100e9, 500e9, nfreq),
+                      f0=300e9, bw=200e9, src_plane=pml + 2,
+                      port_planes=(pml + 6, nx - pml - 6),
+                      name=f"batch {nx}x{ny}x{nz} w{w} h{sub}")
+
+
+def config_batched(n: int = 256, seed: int = 0x220804371, nsteps: int = 20_000) -> List[Problem]:
+    rng = SplitMix64(seed)
+    return [batch_instance(rng, nsteps=nsteps) for _ in range(n)]
+
+
+def config_long_run(nsteps: int = 1_000_000, ringing: bool = False, nfreq: int = 256) -> Problem:
+    """Long-run precision study: 256x128x128 lossless eps_r 3.9 microstrip (5 um cells),
+    256 DFT frequencies.  The ringing variant closes both x ends with PEC so the line
+    keeps resonating and the DFT accumulators keep growing."""
+    bc = (BC_PEC, BC_PEC, BC_PML, BC_PML, BC_PEC, BC_PML) if ringing else \
+         (BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML)
+    return microstrip(256, 128, 128, 5e-6, sub_cells=16, strip_j0=52, strip_j1=76, eps_r=3.9,
+                      sigma=0.0, pml=8, bc=bc, courant=0.99, nsteps=nsteps,
+                      freqs=linear_freqs(100e9, 500e9, nfreq), f0=300e9, bw=200e9,
+                      src_plane=10, port_planes=(14, 256 - 14),
+                      name="long-run 256x128x128" + (" ringing" if ringing else ""))
+
+
+def surrogate_inputs(rng: SplitMix64, n: int) -> np.ndarray:
+    """Line descriptors for the surrogate: (width cells 4-40, thickness cells 0-10,
+    substrate cells 6-30, eps_r 2-12, sigma S/m 0-50, length cells 32-160)."""
+    out = np.zeros((n, 6), dtype=np.float64)
+    for r in range(n):
+        out[r] = (rng.randint(4, 40), rng.randint(0, 10), rng.randint(6, 30),
+                  rng.uniform(2.0, 12.0), rng.uniform(0.0, 50.0), rng.randint(32, 160))
+    return out
+
+
+def random_fields(shape_zyx: tuple, seed: int) -> np.ndarray:
+    """Six seeded random component arrays of shape (nz+1, ny+1, nx+1), values in [-1, 1)."""
+    rng = SplitMix64(seed)
+    n = int(np.prod(shape_zyx))
+    vals = np.array([rng.uniform(-1.0, 1.0) for _ in range(6 * n)], dtype=np.float64)
+    return vals.reshape((6,) + tuple(shape_zyx))
