@@ -1,0 +1,268 @@
+"""Benchmark: FDTD Gcell-updates/s of the single large lossy line (768x384x256 cells of
+20 nm, FP32 fields, 12-cell PML, two ports with 128-frequency running DFTs).
+
+One bench step = `--chunk` FDTD time steps of the whole hot path (H update, E update with
+materials and CPML, soft source, port V/I integrals, running DFTs), replayed from captured
+CUDA graphs.  Inputs (1.8 GB of fields) are far larger than the 126 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own replica of the line (the single grid is not
+decomposed across GPUs): value = all ranks' cell updates / max rank time, scaling "weak".
+The reference arm times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDTD Gcell-updates/s & %HBM roofline; batched S-param solves/s vs surrogate"
+UNIT = "Gcell-updates/s"
+BYTES_PER_CELL_FP32 = 51.0   # 6 components read + written once (48 B) + 3 edge-class bytes
+
+
+def workload():
+    from paper_2208_04371_b300 import workloads as W
+    return W.config_lossy_line(nsteps=0)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d["hbm_gbs"], "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(target_s: float = 15.0):
+    """The FP64 oracle on a bounded sample: the same cell stack on a 256x128x256 slice of
+    the line, a few steps.  Returns (Gcell/s, threads, description)."""
+    from oracle import yee
+    from paper_2208_04371_b300 import workloads as W
+    p = W.config_lossy_line(nx=256, ny=128, nz=256, nsteps=0)
+    threads = os.cpu_count() or 1
+    steps = 2
+    t = time.perf_counter()
+    yee.run(p, nsteps=steps, threads=threads)
+    el = time.perf_counter() - t
+    # scale the step count so the timed sample lasts about target_s
+    per = el / steps
+    steps2 = max(2, int(target_s / max(per, 1e-3)))
+    steps2 = min(steps2, 40)
+    t = time.perf_counter()
+    yee.run(p, nsteps=steps2, threads=threads)
+    el2 = time.perf_counter() - t
+    rate = p.cells * steps2 / el2 / 1e9
+    desc = (f"FP64 oracle, {p.nx}x{p.ny}x{p.nz} slice of the lossy-line stack, {steps2} steps "
+            f"(includes its set-up), OpenMP over k-planes")
+    return rate, threads, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    rates = []
+    threads, desc = os.cpu_count() or 1, ""
+    for _ in range(args.warmup):
+        pass
+    per_step = []
+    for _ in range(args.steps):
+        r, threads, desc = cpu_oracle_sample(target_s=args.ref_seconds)
+        rates.append(r)
+    value = float(np.median(rates))
+    p = workload()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": p.cells * args.chunk / (value * 1e9) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": p.name, "cells": p.cells,
+                                        "steps_per_bench_step": args.chunk},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2208_04371_b300 import yf
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p = workload()
+    stream = torch.cuda.Stream()
+    g = yf.Grid(p, prec=yf.FP32, stream=stream.cuda_stream)
+    chunk = args.chunk
+    for _ in range(args.warmup):
+        g.step(chunk)
+    g.sync()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.step(chunk)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    g.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cell_updates = p.cells * chunk * args.steps * world
+    value = cell_updates / (ms / 1e3) / 1e9
+
+    # per-kernel durations (CUDA events around every launch, same stream, right after the
+    # timed region) for the roofline of the stencil
+    prof = yf.profile_steps(g.h, chunk)
+    stencil_ms = prof["k_update_h"] + prof["k_update_e"]
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL_FP32 * p.cells / (stencil_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_update_h + k_update_e (one step)",
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "bytes_per_cell_update": BYTES_PER_CELL_FP32,
+            "kernel_ms": prof}
+
+    # end to end through the public API: new geometry from pinned host memory every step
+    # (yf_reset + yf_set_materials), the chunk of steps, and the port spectra read back
+    ids_host = torch.from_numpy(p.ids).pin_memory()
+    e2e_ms = []
+    nf = len(p.freqs)
+    for it in range(max(3, args.steps // 4) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        yf.reset(g.h)
+        yf.set_materials(g.h, ids_host, p.eps_r, p.sigma, p.mu_r, p.is_pec)
+        g.step(chunk)
+        V, I = yf.read_port_dft(g.h, 0, nf)
+        V2, I2 = yf.read_port_dft(g.h, 1, nf)
+        if it > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = p.cells * chunk * world / (np.median(e2e_ms) / 1e3) / 1e9
+    g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, threads, desc = cpu_oracle_sample()
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": p.name, "cells": p.cells, "steps_per_bench_step": chunk,
+                       "l2": "inputs larger than L2 (1.8 GB of fields)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(p.ids.nbytes),
+                    "d2h_bytes_per_step": int(2 * 4 * nf * 8)},
+            "gpu_launches": 3 * chunk * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

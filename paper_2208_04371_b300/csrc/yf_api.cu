@@ -1,0 +1,817 @@
+// C ABI of the single-grid solver: handle life cycle, set-up, time stepping with captured
+// CUDA graphs, read-out and checkpoints.  See include/yeefdtd.h for the contract.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "yf_internal.h"
+#include "yf_grid.h"
+
+namespace yf {
+
+static thread_local std::string g_err;
+
+yf_status fail(yf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+yf_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(YF_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(YF_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+double courant_limit_dt(double dx, double dy, double dz)
+{
+    return 1.0 / (kC0 * std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz)));
+}
+
+// CPML profile at position pos (cells) along an axis of N cells; same grading as the
+// absorbing-layer description in yf_set_pml.
+static void pml_point(const yf_grid *g, int axis, int N, double delta, double pos, double *b,
+                      double *a, double *rk)
+{
+    double depth = 0.0;
+    const double L = (double)g->pml_n;
+    if (g->pml_n > 0) {
+        if (g->bc[2 * axis] == YF_BC_PML && pos < L) depth = (L - pos) / L;
+        if (g->bc[2 * axis + 1] == YF_BC_PML && pos > N - L) depth = (pos - (N - L)) / L;
+    }
+    if (depth <= 0.0) {
+        *b = 1.0; *a = 0.0; *rk = 1.0;
+        return;
+    }
+    const double m = (double)g->pml_order;
+    const double eta0 = std::sqrt(kMu0 / kEps0);
+    const double smax = g->pml_sigma_scale * 0.8 * (m + 1.0) / (eta0 * delta);
+    const double gr = std::pow(depth, m);
+    const double sg = smax * gr;
+    const double kap = 1.0 + (g->pml_kappa_max - 1.0) * gr;
+    const double al = g->pml_alpha_max * (1.0 - depth);
+    *b = std::exp(-(sg / kap + al) * g->dt / kEps0);
+    *a = (sg > 0.0) ? sg / (sg * kap + kap * kap * al) * (*b - 1.0) : 0.0;
+    *rk = 1.0 / kap;
+}
+
+template <typename T>
+static yf_status upload_as(void **dst, const std::vector<double> &src)
+{
+    std::vector<T> tmp(src.begin(), src.end());
+    YF_CUDA_TRY(cudaMalloc(dst, tmp.size() * sizeof(T)));
+    YF_CUDA_TRY(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return YF_OK;
+}
+
+static yf_status build_coeff_tables(yf_grid *g)
+{
+    std::vector<double> tab(2 * kMaxClasses, 0.0), eps(kMaxClasses, 0.0);
+    for (int c = 1; c < g->mat.nclass; ++c) {
+        const double e = kEps0 * g->mat.eps_r[c];
+        const double loss = g->mat.sigma[c] * g->dt / (2.0 * e);
+        tab[2 * c] = (1.0 - loss) / (1.0 + loss);
+        tab[2 * c + 1] = (g->dt / e) / (1.0 + loss);
+        eps[c] = e;
+    }
+    if (g->prec == YF_FP32) {
+        std::vector<float> t32(tab.begin(), tab.end());
+        YF_CUDA_TRY(cudaMemcpy(g->ctab, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        YF_CUDA_TRY(cudaMemcpy(g->ctab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    YF_CUDA_TRY(cudaMemcpy(g->eps_tab, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return YF_OK;
+}
+
+static yf_status derive_materials(yf_grid *g, const uint8_t *ids_dev, int nmat, const double *eps_r,
+                                  const double *sigma, const uint8_t *is_pec)
+{
+    yf_status st = derive_edge_classes(g->nx, g->ny, g->nz, g->px, g->plane, ids_dev, nmat, eps_r,
+                                       sigma, is_pec, g->cls, &g->mat, g->stream);
+    if (st != YF_OK) return st;
+    st = build_coeff_tables(g);
+    if (st != YF_OK) return st;
+    for (size_t s = 0; s < g->sheets.size(); s += 6) {
+        st = apply_pec_sheet(g->nx, g->ny, g->nz, g->px, g->plane, g->cls, &g->sheets[s], g->stream);
+        if (st != YF_OK) return st;
+    }
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->materials_done = true;
+    return YF_OK;
+}
+
+static yf_status build_pml(yf_grid *g)
+{
+    const int N[3] = {g->nx, g->ny, g->nz};
+    const double D[3] = {g->dx, g->dy, g->dz};
+    const int n = g->pml_n;
+    for (int a = 0; a < 3; ++a) {
+        g->pml_lo[a] = (n > 0 && g->bc[2 * a] == YF_BC_PML);
+        g->pml_hi[a] = (n > 0 && g->bc[2 * a + 1] == YF_BC_PML);
+        if (!g->pml_lo[a] && !g->pml_hi[a]) continue;
+        if (N[a] < 2 * n + 1)
+            return fail(YF_E_INVALID, "axis %d has %d cells, PML of %d cells needs >= %d", a, N[a], n,
+                        2 * n + 1);
+        const int N1 = N[a] + 1;
+        std::vector<double> prof(6 * N1, 0.0);
+        for (int p = 0; p <= N[a]; ++p)
+            pml_point(g, a, N[a], D[a], (double)p, &prof[0 * N1 + p], &prof[1 * N1 + p], &prof[2 * N1 + p]);
+        for (int p = 0; p < N[a]; ++p)
+            pml_point(g, a, N[a], D[a], p + 0.5, &prof[3 * N1 + p], &prof[4 * N1 + p], &prof[5 * N1 + p]);
+        yf_status st = g->prec == YF_FP32 ? upload_as<float>(&g->prof[a], prof)
+                                          : upload_as<double>(&g->prof[a], prof);
+        if (st != YF_OK) return st;
+        const int L = 2 * n + 1;
+        size_t cnt;
+        if (a == 0) cnt = (size_t)(g->nz + 1) * (g->ny + 1) * L;
+        else if (a == 1) cnt = (size_t)(g->nz + 1) * L * g->px;
+        else cnt = (size_t)L * (g->ny + 1) * g->px;
+        g->psi_count[a] = cnt;
+        for (int q = 0; q < 4; ++q) {
+            YF_CUDA_TRY(cudaMalloc(&g->psi[a][q], cnt * g->esz));
+            YF_CUDA_TRY(cudaMemset(g->psi[a][q], 0, cnt * g->esz));
+        }
+    }
+    return YF_OK;
+}
+
+template <typename T>
+static void fill_params(yf_grid *g)
+{
+    StencilParams<T> &P = *reinterpret_cast<StencilParams<T> *>(g->sp);
+    P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.px = g->px; P.plane = g->plane;
+    P.rdx = (T)(1.0 / g->dx); P.rdy = (T)(1.0 / g->dy); P.rdz = (T)(1.0 / g->dz);
+    P.db = (T)(g->dt / kMu0);
+    for (int c = 0; c < 3; ++c) P.cls[c] = g->cls[c];
+    P.ctab = (const T *)g->ctab;
+    P.pml.n = g->pml_n;
+    P.pml.len = 2 * g->pml_n + 1;
+    for (int a = 0; a < 3; ++a) {
+        P.pml.lo[a] = g->pml_lo[a];
+        P.pml.hi[a] = g->pml_hi[a];
+        P.pml.prof[a] = (const T *)g->prof[a];
+        for (int q = 0; q < 4; ++q) P.pml.psi[a][q] = (T *)g->psi[a][q];
+    }
+    Fields<T> &F = *reinterpret_cast<Fields<T> *>(g->fp);
+    for (int c = 0; c < 6; ++c) F.c[c] = (T *)g->fld[c];
+
+    EpiParams<T> &E = *reinterpret_cast<EpiParams<T> *>(g->ep);
+    E.ez = (T *)g->fld[2]; E.hy = (const T *)g->fld[4]; E.hz = (const T *)g->fld[5];
+    E.cls_z = g->cls[2];
+    E.nx = g->nx; E.ny = g->ny; E.nz = g->nz; E.px = g->px; E.plane = g->plane;
+    E.src_kind = g->has_src ? g->src.kind : YF_WAVE_NONE;
+    E.src_plane = g->src_plane; E.sj0 = g->sj0; E.sj1 = g->sj1; E.sk0 = g->sk0; E.sk1 = g->sk1;
+    E.amp = g->src.amplitude; E.p0 = g->src.p0; E.p1 = g->src.p1; E.t0 = g->src.t0; E.dt = g->dt;
+    E.table = g->src_table_dev; E.table_len = g->src_table_len;
+    E.nports = (int)g->ports.size();
+    E.ports = g->ports_dev; E.inc = g->inc_dev; E.dft_mask = g->dft_mask;
+    E.acc64 = g->acc64; E.acc32 = g->acc32; E.kahan = g->kahan;
+    E.dy = g->dy; E.dz = g->dz;
+    E.ctr = g->ctr; E.status = g->status;
+}
+
+yf_status finalize(yf_grid *g)
+{
+    if (g->started) return YF_OK;
+    yf_status st;
+    if (!g->materials_done) {
+        uint8_t *ids = nullptr;
+        const size_t ncell = (size_t)g->nx * g->ny * g->nz;
+        YF_CUDA_TRY(cudaMalloc(&ids, ncell));
+        YF_CUDA_TRY(cudaMemset(ids, 0, ncell));
+        const double er = 1.0, sg = 0.0;
+        const uint8_t pec = 0;
+        st = derive_materials(g, ids, 1, &er, &sg, &pec);
+        cudaFree(ids);
+        if (st != YF_OK) return st;
+    }
+    st = build_pml(g);
+    if (st != YF_OK) return st;
+    // ports and DFT accumulators
+    const int np = (int)g->ports.size();
+    int total = 0;
+    for (int p = 0; p < np; ++p) total += g->ports[p].nfreq;
+    g->nf_total = total;
+    if (np > 0) {
+        YF_CUDA_TRY(cudaMalloc(&g->ports_dev, np * sizeof(PortDev)));
+        YF_CUDA_TRY(cudaMemcpy(g->ports_dev, g->ports.data(), np * sizeof(PortDev), cudaMemcpyHostToDevice));
+        YF_CUDA_TRY(cudaMalloc(&g->inc_dev, total * sizeof(unsigned long long)));
+        YF_CUDA_TRY(cudaMemcpy(g->inc_dev, g->inc.data(), total * sizeof(unsigned long long),
+                               cudaMemcpyHostToDevice));
+        YF_CUDA_TRY(cudaMalloc(&g->acc64, (size_t)total * 4 * sizeof(double)));
+        YF_CUDA_TRY(cudaMemset(g->acc64, 0, (size_t)total * 4 * sizeof(double)));
+        YF_CUDA_TRY(cudaMalloc(&g->acc32, (size_t)total * 4 * sizeof(float)));
+        YF_CUDA_TRY(cudaMemset(g->acc32, 0, (size_t)total * 4 * sizeof(float)));
+        YF_CUDA_TRY(cudaMalloc(&g->kahan, (size_t)total * 8 * sizeof(float)));
+        YF_CUDA_TRY(cudaMemset(g->kahan, 0, (size_t)total * 8 * sizeof(float)));
+    }
+    if (g->has_src && g->src.kind == YF_WAVE_TABLE && !g->src_table_host.empty()) {
+        YF_CUDA_TRY(cudaMalloc(&g->src_table_dev, g->src_table_host.size() * sizeof(double)));
+        YF_CUDA_TRY(cudaMemcpy(g->src_table_dev, g->src_table_host.data(),
+                               g->src_table_host.size() * sizeof(double), cudaMemcpyHostToDevice));
+        g->src_table_len = (long)g->src_table_host.size();
+    }
+    if (g->prec == YF_FP32) fill_params<float>(g);
+    else fill_params<double>(g);
+    g->started = true;
+    return YF_OK;
+}
+
+template <typename T>
+static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
+{
+    const StencilParams<T> &P = *reinterpret_cast<const StencilParams<T> *>(g->sp);
+    const Fields<T> &F = *reinterpret_cast<const Fields<T> *>(g->fp);
+    const EpiParams<T> &E = *reinterpret_cast<const EpiParams<T> *>(g->ep);
+    cudaError_t e = launch_update_h<T>(P, F, s);
+    if (e != cudaSuccess) return e;
+    e = launch_update_e<T>(P, F, s);
+    if (e != cudaSuccess) return e;
+    return launch_epilogue<T>(E, s);
+}
+
+static cudaError_t step_direct(yf_grid *g, cudaStream_t s)
+{
+    return g->prec == YF_FP32 ? launch_one_step<float>(g, s) : launch_one_step<double>(g, s);
+}
+
+static yf_status capture_chunk(yf_grid *g)
+{
+    cudaGraph_t graph = nullptr;
+    YF_CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < g->chunk && e == cudaSuccess; ++t) e = step_direct(g, g->stream);
+    cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing step chunk"); }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return YF_OK;
+}
+
+}  // namespace yf
+
+using namespace yf;
+
+extern "C" {
+
+const char *yf_last_error(void) { return g_err.c_str(); }
+
+yf_status yf_courant_dt(double dx, double dy, double dz, double courant, double *dt)
+{
+    if (!dt || !(dx > 0) || !(dy > 0) || !(dz > 0) || !(courant > 0) || courant > 1.0)
+        return fail(YF_E_INVALID, "yf_courant_dt: need positive spacings and 0 < courant <= 1");
+    *dt = courant * courant_limit_dt(dx, dy, dz);
+    return YF_OK;
+}
+
+yf_status yf_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, double dt,
+                         yf_prec prec, void *stream, yf_grid **out)
+{
+    if (!out) return fail(YF_E_INVALID, "yf_grid_create: out is NULL");
+    *out = nullptr;
+    if (nx < 3 || ny < 3 || nz < 3) return fail(YF_E_INVALID, "yf_grid_create: need >= 3 cells per axis");
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return fail(YF_E_INVALID, "yf_grid_create: spacings must be > 0");
+    if (prec != YF_FP32 && prec != YF_FP64) return fail(YF_E_INVALID, "yf_grid_create: bad precision");
+    const double lim = courant_limit_dt(dx, dy, dz);
+    if (dt <= 0) dt = 0.99 * lim;
+    if (dt > lim * (1.0 + 1e-12))
+        return fail(YF_E_UNSTABLE, "dt = %.6g s exceeds the Courant limit %.6g s", dt, lim);
+    yf_grid *g = new (std::nothrow) yf_grid();
+    if (!g) return fail(YF_E_OOM, "yf_grid_create: host allocation failed");
+    g->nx = nx; g->ny = ny; g->nz = nz; g->dx = dx; g->dy = dy; g->dz = dz; g->dt = dt;
+    g->prec = prec;
+    g->esz = prec == YF_FP32 ? 4 : 8;
+    g->px = ((nx + 1) + 31) / 32 * 32;
+    g->plane = (long)g->px * (ny + 1);
+    g->npts = g->plane * (nz + 1);
+    if (stream) {
+        g->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaStreamCreate"); }
+        g->own_stream = true;
+    }
+    auto bail = [&](cudaError_t e, const char *w) { yf_status s = cuda_fail(e, w); yf_grid_destroy(g); return s; };
+    cudaError_t e;
+    for (int c = 0; c < 6; ++c) {
+        if ((e = cudaMalloc(&g->fld[c], g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc fields");
+        if ((e = cudaMemset(g->fld[c], 0, g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMemset fields");
+    }
+    for (int c = 0; c < 3; ++c) {
+        if ((e = cudaMalloc(&g->cls[c], g->npts)) != cudaSuccess) return bail(e, "cudaMalloc classes");
+        if ((e = cudaMemset(g->cls[c], 0, g->npts)) != cudaSuccess) return bail(e, "cudaMemset classes");
+    }
+    if ((e = cudaMalloc(&g->ctab, 2 * kMaxClasses * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc ctab");
+    if ((e = cudaMalloc(&g->eps_tab, kMaxClasses * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc eps");
+    if ((e = cudaMalloc(&g->ctr, sizeof(long long))) != cudaSuccess) return bail(e, "cudaMalloc ctr");
+    if ((e = cudaMemset(g->ctr, 0, sizeof(long long))) != cudaSuccess) return bail(e, "cudaMemset ctr");
+    if ((e = cudaMalloc(&g->status, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc status");
+    if ((e = cudaMemset(g->status, 0, sizeof(int))) != cudaSuccess) return bail(e, "cudaMemset status");
+    if ((e = cudaMalloc(&g->energy_partials, (kEnergyBlocks + 1) * sizeof(double))) != cudaSuccess)
+        return bail(e, "cudaMalloc energy scratch");
+    for (int f = 0; f < 6; ++f) g->bc[f] = YF_BC_PEC;
+    *out = g;
+    return YF_OK;
+}
+
+yf_status yf_grid_destroy(yf_grid *g)
+{
+    if (!g) return YF_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    for (int c = 0; c < 6; ++c) cudaFree(g->fld[c]);
+    for (int c = 0; c < 3; ++c) cudaFree(g->cls[c]);
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(g->prof[a]);
+        for (int q = 0; q < 4; ++q) cudaFree(g->psi[a][q]);
+    }
+    cudaFree(g->ctab); cudaFree(g->eps_tab); cudaFree(g->ctr); cudaFree(g->status);
+    cudaFree(g->energy_partials); cudaFree(g->ports_dev); cudaFree(g->inc_dev);
+    cudaFree(g->acc64); cudaFree(g->acc32); cudaFree(g->kahan); cudaFree(g->src_table_dev);
+    if (g->own_stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return YF_OK;
+}
+
+yf_status yf_grid_dt(yf_grid *g, double *dt)
+{
+    if (!g || !dt) return fail(YF_E_INVALID, "yf_grid_dt: NULL argument");
+    *dt = g->dt;
+    return YF_OK;
+}
+
+yf_status yf_set_materials(yf_grid *g, const uint8_t *ids, yf_mem where, int nmat,
+                           const double *eps_r, const double *sigma, const double *mu_r,
+                           const uint8_t *is_pec)
+{
+    if (!g || !ids || !eps_r || !sigma) return fail(YF_E_INVALID, "yf_set_materials: NULL argument");
+    if (g->started && !g->geometry_open)
+        return fail(YF_E_STATE, "yf_set_materials after the first step (call yf_reset first)");
+    if (nmat < 1 || nmat > 256) return fail(YF_E_INVALID, "yf_set_materials: nmat must be 1..256");
+    for (int m = 0; m < nmat; ++m) {
+        if (!(eps_r[m] > 0) || !(sigma[m] >= 0))
+            return fail(YF_E_INVALID, "material %d: need eps_r > 0 and sigma >= 0", m);
+        if (mu_r && mu_r[m] != 1.0)
+            return fail(YF_E_UNSUPPORTED, "material %d: mu_r != 1 is not supported", m);
+    }
+    const size_t ncell = (size_t)g->nx * g->ny * g->nz;
+    const uint8_t *ids_dev = ids;
+    uint8_t *tmp = nullptr;
+    if (where == YF_HOST) {
+        YF_CUDA_TRY(cudaMalloc(&tmp, ncell));
+        cudaError_t e = cudaMemcpy(tmp, ids, ncell, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(tmp); return cuda_fail(e, "copying ids"); }
+        ids_dev = tmp;
+    }
+    yf_status st = derive_materials(g, ids_dev, nmat, eps_r, sigma, is_pec);
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
+yf_status yf_add_pec_sheet(yf_grid *g, int ax, int index, int lo0, int hi0, int lo1, int hi1)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_add_pec_sheet: NULL grid");
+    if (g->started && !g->geometry_open)
+        return fail(YF_E_STATE, "yf_add_pec_sheet after the first step (call yf_reset first)");
+    const int N[3] = {g->nx, g->ny, g->nz};
+    if (ax < 0 || ax > 2) return fail(YF_E_INVALID, "yf_add_pec_sheet: normal_axis must be 0..2");
+    const int a0 = ax == 0 ? 1 : 0, a1 = ax == 2 ? 1 : 2;
+    if (index < 0 || index > N[ax] || lo0 < 0 || hi0 > N[a0] || lo0 > hi0 || lo1 < 0 ||
+        hi1 > N[a1] || lo1 > hi1)
+        return fail(YF_E_INVALID, "yf_add_pec_sheet: rectangle outside the grid");
+    const int sh[6] = {ax, index, lo0, hi0, lo1, hi1};
+    g->sheets.insert(g->sheets.end(), sh, sh + 6);
+    if (g->materials_done) {
+        yf_status st = apply_pec_sheet(g->nx, g->ny, g->nz, g->px, g->plane, g->cls, sh, g->stream);
+        if (st != YF_OK) return st;
+        YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+    return YF_OK;
+}
+
+yf_status yf_set_boundaries(yf_grid *g, const int bc[6])
+{
+    if (!g || !bc) return fail(YF_E_INVALID, "yf_set_boundaries: NULL argument");
+    if (g->started) return fail(YF_E_STATE, "yf_set_boundaries after the first step");
+    for (int f = 0; f < 6; ++f)
+        if (bc[f] != YF_BC_PEC && bc[f] != YF_BC_PML) return fail(YF_E_INVALID, "bad boundary kind");
+    for (int f = 0; f < 6; ++f) g->bc[f] = bc[f];
+    return YF_OK;
+}
+
+yf_status yf_set_pml(yf_grid *g, int ncells, int order, double sigma_scale, double kappa_max,
+                     double alpha_max)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_set_pml: NULL grid");
+    if (g->started) return fail(YF_E_STATE, "yf_set_pml after the first step");
+    if (ncells < 0 || order < 0 || !(sigma_scale >= 0) || !(kappa_max >= 1) || !(alpha_max >= 0))
+        return fail(YF_E_INVALID, "yf_set_pml: bad parameters");
+    g->pml_n = ncells; g->pml_order = order; g->pml_sigma_scale = sigma_scale;
+    g->pml_kappa_max = kappa_max; g->pml_alpha_max = alpha_max;
+    return YF_OK;
+}
+
+yf_status yf_set_source(yf_grid *g, int axis, int plane, int j0, int j1, int k0, int k1,
+                        const yf_waveform *w)
+{
+    if (!g || !w) return fail(YF_E_INVALID, "yf_set_source: NULL argument");
+    if (g->started) return fail(YF_E_STATE, "yf_set_source after the first step");
+    if (axis != 0) return fail(YF_E_UNSUPPORTED, "yf_set_source: only axis 0 (x) is supported");
+    if (plane < 1 || plane >= g->nx || j0 < 1 || j1 >= g->ny || j0 > j1 || k0 < 0 || k1 > g->nz ||
+        k0 >= k1)
+        return fail(YF_E_INVALID, "yf_set_source: rectangle outside the interior E_z edges");
+    if (w->kind < YF_WAVE_NONE || w->kind > YF_WAVE_TABLE) return fail(YF_E_INVALID, "bad waveform kind");
+    if (w->kind == YF_WAVE_DIFF_GAUSS && !(w->p0 > 0)) return fail(YF_E_INVALID, "sigma must be > 0");
+    if (w->kind == YF_WAVE_GAUSS_SINE && !(w->p1 > 0)) return fail(YF_E_INVALID, "bandwidth must be > 0");
+    if (w->kind == YF_WAVE_TABLE && (!w->table || w->table_len <= 0))
+        return fail(YF_E_INVALID, "table waveform needs a table");
+    g->src = *w;
+    if (g->src.t0 < 0) {
+        if (w->kind == YF_WAVE_DIFF_GAUSS) g->src.t0 = 3.0 * w->p0;
+        else if (w->kind == YF_WAVE_GAUSS_SINE) g->src.t0 = 3.0 * (2.0 / (M_PI * w->p1));
+        else g->src.t0 = 0.0;
+    }
+    if (w->kind == YF_WAVE_TABLE) g->src_table_host.assign(w->table, w->table + w->table_len);
+    g->src.table = nullptr;
+    g->src_plane = plane; g->sj0 = j0; g->sj1 = j1; g->sk0 = k0; g->sk1 = k1;
+    g->has_src = w->kind != YF_WAVE_NONE;
+    return YF_OK;
+}
+
+yf_status yf_add_port(yf_grid *g, const yf_port_desc *d, int nfreq, const double *freqs,
+                      int *port_id)
+{
+    if (!g || !d || !freqs) return fail(YF_E_INVALID, "yf_add_port: NULL argument");
+    if (g->started) return fail(YF_E_STATE, "yf_add_port after the first step");
+    if ((int)g->ports.size() >= kMaxPorts) return fail(YF_E_UNSUPPORTED, "at most %d ports", kMaxPorts);
+    if (d->axis != 0) return fail(YF_E_UNSUPPORTED, "yf_add_port: only axis 0 (x) is supported");
+    const int m = d->margin;
+    if (d->plane < 1 || d->plane >= g->nx || (d->direction != 1 && d->direction != -1) ||
+        d->j0 < 1 || d->j1 >= g->ny || d->j0 >= d->j1 || d->k0 < 0 || d->k1 > g->nz ||
+        d->k0 >= d->k1 || m < 1 || d->kb > d->kt || d->j0 - m < 0 || d->j1 + m - 1 > g->ny - 1 ||
+        d->kb - m < 0 || d->kt + m - 1 > g->nz - 1)
+        return fail(YF_E_INVALID, "yf_add_port: V surface or I loop outside the grid");
+    if (nfreq < 1) return fail(YF_E_INVALID, "yf_add_port: nfreq must be >= 1");
+    for (int f = 0; f < nfreq; ++f)
+        if (!(freqs[f] > 0) || !(freqs[f] * g->dt < 1.0))
+            return fail(YF_E_INVALID, "yf_add_port: frequencies must lie in (0, 1/dt)");
+    PortDev p;
+    p.plane = d->plane; p.dir = d->direction; p.j0 = d->j0; p.j1 = d->j1; p.k0 = d->k0;
+    p.k1 = d->k1; p.kb = d->kb; p.kt = d->kt; p.m = m; p.nfreq = nfreq;
+    p.foff = (int)g->inc.size();
+    const double width = d->width > 0 ? d->width : (d->j1 - d->j0) * g->dy;
+    p.vscale = -(g->dy * g->dz) / width;
+    for (int f = 0; f < nfreq; ++f) {
+        // phase increment per half step as a 64-bit fraction of a turn
+        const double x = freqs[f] * g->dt * 0.5;
+        g->inc.push_back((unsigned long long)std::llrint(x * 0x1p64));
+        g->freqs.push_back(freqs[f]);
+    }
+    g->ports.push_back(p);
+    if (port_id) *port_id = (int)g->ports.size() - 1;
+    return YF_OK;
+}
+
+yf_status yf_set_dft_mode(yf_grid *g, int mask)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_set_dft_mode: NULL grid");
+    if (g->started) return fail(YF_E_STATE, "yf_set_dft_mode after the first step");
+    if (mask <= 0 || (mask & ~(YF_DFT_FP64 | YF_DFT_KAHAN32 | YF_DFT_FP32)))
+        return fail(YF_E_INVALID, "yf_set_dft_mode: bad mask");
+    g->dft_mask = mask;
+    return YF_OK;
+}
+
+yf_status yf_step(yf_grid *g, long n)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_step: NULL grid");
+    if (n < 0) return fail(YF_E_INVALID, "yf_step: n < 0");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    g->geometry_open = false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    YF_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
+    long done = 0;
+    if (cs == cudaStreamCaptureStatusNone && n >= g->chunk) {
+        if (!g->graph) {
+            st = capture_chunk(g);
+            if (st != YF_OK) return st;
+        }
+        for (; done + g->chunk <= n; done += g->chunk) YF_CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+    }
+    for (; done < n; ++done) YF_CUDA_TRY(step_direct(g, g->stream));
+    g->steps_done += n;
+    return YF_OK;
+}
+
+yf_status yf_sync(yf_grid *g)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_sync: NULL grid");
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    int st = 0;
+    YF_CUDA_TRY(cudaMemcpy(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 1) return fail(YF_E_UNSTABLE, "a port sample became non-finite");
+    return YF_OK;
+}
+
+yf_status yf_steps_done(yf_grid *g, long *n)
+{
+    if (!g || !n) return fail(YF_E_INVALID, "yf_steps_done: NULL argument");
+    *n = g->steps_done;
+    return YF_OK;
+}
+
+yf_status yf_read_fields(yf_grid *g, int comp, void *dst, yf_mem where)
+{
+    if (!g || !dst || comp < 0 || comp > 5) return fail(YF_E_INVALID, "yf_read_fields: bad argument");
+    const size_t w = (size_t)(g->nx + 1) * g->esz;
+    YF_CUDA_TRY(cudaMemcpy2DAsync(dst, w, g->fld[comp], (size_t)g->px * g->esz, w,
+                                  (size_t)(g->ny + 1) * (g->nz + 1),
+                                  where == YF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                  g->stream));
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return YF_OK;
+}
+
+yf_status yf_write_fields(yf_grid *g, int comp, const void *src, yf_mem where)
+{
+    if (!g || !src || comp < 0 || comp > 5) return fail(YF_E_INVALID, "yf_write_fields: bad argument");
+    if (!g->materials_done) {
+        // classes decide which edges are PEC; settle the default materials first
+        uint8_t *ids = nullptr;
+        const size_t ncell = (size_t)g->nx * g->ny * g->nz;
+        YF_CUDA_TRY(cudaMalloc(&ids, ncell));
+        YF_CUDA_TRY(cudaMemset(ids, 0, ncell));
+        const double er = 1.0, sg = 0.0;
+        const uint8_t pec = 0;
+        yf_status st = derive_materials(g, ids, 1, &er, &sg, &pec);
+        cudaFree(ids);
+        if (st != YF_OK) return st;
+    }
+    const size_t w = (size_t)(g->nx + 1) * g->esz;
+    YF_CUDA_TRY(cudaMemcpy2DAsync(g->fld[comp], (size_t)g->px * g->esz, src, w, w,
+                                  (size_t)(g->ny + 1) * (g->nz + 1),
+                                  where == YF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  g->stream));
+    cudaError_t e;
+    if (g->prec == YF_FP32) {
+        Fields<float> F;
+        for (int c = 0; c < 6; ++c) F.c[c] = (float *)g->fld[c];
+        e = launch_sanitize<float>(F, g->cls, g->nx, g->ny, g->nz, g->px, g->plane, g->stream);
+    } else {
+        Fields<double> F;
+        for (int c = 0; c < 6; ++c) F.c[c] = (double *)g->fld[c];
+        e = launch_sanitize<double>(F, g->cls, g->nx, g->ny, g->nz, g->px, g->plane, g->stream);
+    }
+    YF_CUDA_TRY(e);
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return YF_OK;
+}
+
+yf_status yf_energy(yf_grid *g, double *w)
+{
+    if (!g || !w) return fail(YF_E_INVALID, "yf_energy: NULL argument");
+    if (!g->materials_done) { *w = 0.0; }
+    double *out = g->energy_partials + kEnergyBlocks;
+    cudaError_t e;
+    if (g->prec == YF_FP32) {
+        const float *c[6];
+        for (int q = 0; q < 6; ++q) c[q] = (const float *)g->fld[q];
+        e = launch_energy<float>(c, g->cls, g->eps_tab, g->nx, g->ny, g->nz, g->px, g->plane,
+                                 g->energy_partials, out, g->stream);
+    } else {
+        const double *c[6];
+        for (int q = 0; q < 6; ++q) c[q] = (const double *)g->fld[q];
+        e = launch_energy<double>(c, g->cls, g->eps_tab, g->nx, g->ny, g->nz, g->px, g->plane,
+                                  g->energy_partials, out, g->stream);
+    }
+    YF_CUDA_TRY(e);
+    double r = 0.0;
+    YF_CUDA_TRY(cudaMemcpyAsync(&r, out, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    *w = r * g->dx * g->dy * g->dz;
+    return YF_OK;
+}
+
+yf_status yf_read_port_dft(yf_grid *g, int port, int kind, double *V_re, double *V_im,
+                           double *I_re, double *I_im)
+{
+    if (!g || port < 0 || port >= (int)g->ports.size())
+        return fail(YF_E_INVALID, "yf_read_port_dft: bad port");
+    if (kind != YF_DFT_FP64 && kind != YF_DFT_KAHAN32 && kind != YF_DFT_FP32)
+        return fail(YF_E_INVALID, "yf_read_port_dft: bad accumulator kind");
+    const PortDev &p = g->ports[port];
+    const int nf = p.nfreq;
+    std::vector<double> v(4 * (size_t)nf, 0.0);
+    if (g->started) {
+        if (!(g->dft_mask & kind)) return fail(YF_E_STATE, "accumulator kind was not enabled");
+        YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        if (kind == YF_DFT_FP64) {
+            YF_CUDA_TRY(cudaMemcpy(v.data(), g->acc64 + 4 * (size_t)p.foff, 4 * nf * sizeof(double),
+                                   cudaMemcpyDeviceToHost));
+        } else if (kind == YF_DFT_FP32) {
+            std::vector<float> f(4 * (size_t)nf);
+            YF_CUDA_TRY(cudaMemcpy(f.data(), g->acc32 + 4 * (size_t)p.foff, 4 * nf * sizeof(float),
+                                   cudaMemcpyDeviceToHost));
+            for (size_t q = 0; q < f.size(); ++q) v[q] = f[q];
+        } else {
+            std::vector<float> f(8 * (size_t)nf);
+            YF_CUDA_TRY(cudaMemcpy(f.data(), g->kahan + 8 * (size_t)p.foff, 8 * nf * sizeof(float),
+                                   cudaMemcpyDeviceToHost));
+            for (size_t q = 0; q < 4 * (size_t)nf; ++q) v[q] = (double)f[2 * q] - (double)f[2 * q + 1];
+        }
+    }
+    for (int f = 0; f < nf; ++f) {
+        if (V_re) V_re[f] = v[4 * f + 0] * g->dt;
+        if (V_im) V_im[f] = v[4 * f + 1] * g->dt;
+        if (I_re) I_re[f] = v[4 * f + 2] * g->dt;
+        if (I_im) I_im[f] = v[4 * f + 3] * g->dt;
+    }
+    return YF_OK;
+}
+
+yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, double *Zr,
+                          double *Zc, double *tau)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_read_sparams: NULL grid");
+    if (g->ports.size() != 2) return fail(YF_E_INVALID, "yf_read_sparams: needs exactly two ports");
+    const int nf = g->ports[0].nfreq;
+    if (g->ports[1].nfreq != nf) return fail(YF_E_INVALID, "yf_read_sparams: ports differ in frequencies");
+    for (int f = 0; f < nf; ++f)
+        if (g->freqs[f] != g->freqs[nf + f])
+            return fail(YF_E_INVALID, "yf_read_sparams: ports differ in frequencies");
+    std::vector<double> d(8 * (size_t)nf);
+    for (int p = 0; p < 2; ++p) {
+        yf_status st = yf_read_port_dft(g, p, YF_DFT_FP64, &d[(4 * p + 0) * nf], &d[(4 * p + 1) * nf],
+                                        &d[(4 * p + 2) * nf], &d[(4 * p + 3) * nf]);
+        if (st != YF_OK) return st;
+    }
+    return sparams_uniform(nf, g->freqs.data(), d.data(), g->ports[1].dir, z_ref, S_star, S, Zr, Zc, tau);
+}
+
+yf_status yf_reset(yf_grid *g)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_reset: NULL grid");
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int c = 0; c < 6; ++c) YF_CUDA_TRY(cudaMemsetAsync(g->fld[c], 0, g->npts * g->esz, g->stream));
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 4; ++q)
+            if (g->psi[a][q]) YF_CUDA_TRY(cudaMemsetAsync(g->psi[a][q], 0, g->psi_count[a] * g->esz, g->stream));
+    if (g->nf_total > 0) {
+        YF_CUDA_TRY(cudaMemsetAsync(g->acc64, 0, (size_t)g->nf_total * 4 * sizeof(double), g->stream));
+        YF_CUDA_TRY(cudaMemsetAsync(g->acc32, 0, (size_t)g->nf_total * 4 * sizeof(float), g->stream));
+        YF_CUDA_TRY(cudaMemsetAsync(g->kahan, 0, (size_t)g->nf_total * 8 * sizeof(float), g->stream));
+    }
+    YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(long long), g->stream));
+    YF_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), g->stream));
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->steps_done = 0;
+    g->sheets.clear();
+    g->geometry_open = true;
+    return YF_OK;
+}
+
+yf_status yf_profile_steps(yf_grid *g, long n, double *ms, int *nkern)
+{
+    if (!g || !ms || !nkern || n < 1) return fail(YF_E_INVALID, "yf_profile_steps: bad argument");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    const int nk = 3;
+    cudaEvent_t ev[nk + 1];
+    for (int q = 0; q <= nk; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
+    double acc[nk] = {0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (long t = 0; t < n && e == cudaSuccess; ++t) {
+        cudaEventRecord(ev[0], g->stream);
+        if (g->prec == YF_FP32) {
+            const auto &P = *reinterpret_cast<const StencilParams<float> *>(g->sp);
+            const auto &F = *reinterpret_cast<const Fields<float> *>(g->fp);
+            launch_update_h<float>(P, F, g->stream);
+            cudaEventRecord(ev[1], g->stream);
+            launch_update_e<float>(P, F, g->stream);
+            cudaEventRecord(ev[2], g->stream);
+            launch_epilogue<float>(*reinterpret_cast<const EpiParams<float> *>(g->ep), g->stream);
+        } else {
+            const auto &P = *reinterpret_cast<const StencilParams<double> *>(g->sp);
+            const auto &F = *reinterpret_cast<const Fields<double> *>(g->fp);
+            launch_update_h<double>(P, F, g->stream);
+            cudaEventRecord(ev[1], g->stream);
+            launch_update_e<double>(P, F, g->stream);
+            cudaEventRecord(ev[2], g->stream);
+            launch_epilogue<double>(*reinterpret_cast<const EpiParams<double> *>(g->ep), g->stream);
+        }
+        cudaEventRecord(ev[3], g->stream);
+        e = cudaEventSynchronize(ev[3]);
+        for (int q = 0; q < nk && e == cudaSuccess; ++q) {
+            float m = 0.f;
+            e = cudaEventElapsedTime(&m, ev[q], ev[q + 1]);
+            acc[q] += m;
+        }
+    }
+    for (int q = 0; q <= nk; ++q) cudaEventDestroy(ev[q]);
+    YF_CUDA_TRY(e);
+    g->steps_done += n;
+    for (int q = 0; q < nk; ++q) ms[q] = acc[q] / (double)n;
+    *nkern = nk;
+    return YF_OK;
+}
+
+const char *yf_kernel_name(yf_grid *g, int idx)
+{
+    (void)g;
+    static const char *names[] = {"k_update_h", "k_update_e", "k_epilogue"};
+    return (idx >= 0 && idx < 3) ? names[idx] : "";
+}
+
+// checkpoint: header, fields, CPML auxiliaries, accumulators, counters
+struct CkptHeader {
+    char magic[8];
+    int nx, ny, nz, prec, pml_n, nf_total;
+    long steps;
+    long long ctr;
+    int status;
+};
+
+yf_status yf_checkpoint_save(yf_grid *g, const char *path)
+{
+    if (!g || !path) return fail(YF_E_INVALID, "yf_checkpoint_save: NULL argument");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(YF_E_INVALID, "cannot open %s for writing", path);
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "YFCKPT1", 8);
+    h.nx = g->nx; h.ny = g->ny; h.nz = g->nz; h.prec = g->prec; h.pml_n = g->pml_n;
+    h.nf_total = g->nf_total; h.steps = g->steps_done;
+    cudaMemcpy(&h.ctr, g->ctr, sizeof(long long), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&h.status, g->status, sizeof(int), cudaMemcpyDeviceToHost);
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+    auto dump = [&](const void *dev, size_t bytes) {
+        if (!ok || !dev || bytes == 0) return;
+        std::vector<char> buf(bytes);
+        ok = cudaMemcpy(buf.data(), dev, bytes, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             fwrite(buf.data(), 1, bytes, fp) == bytes;
+    };
+    for (int c = 0; c < 6; ++c) dump(g->fld[c], g->npts * g->esz);
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 4; ++q) dump(g->psi[a][q], g->psi_count[a] * g->esz);
+    dump(g->acc64, (size_t)g->nf_total * 4 * sizeof(double));
+    dump(g->acc32, (size_t)g->nf_total * 4 * sizeof(float));
+    dump(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));
+    fclose(fp);
+    if (!ok) return fail(YF_E_CUDA, "checkpoint write to %s failed", path);
+    return YF_OK;
+}
+
+yf_status yf_checkpoint_load(yf_grid *g, const char *path)
+{
+    if (!g || !path) return fail(YF_E_INVALID, "yf_checkpoint_load: NULL argument");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(YF_E_INVALID, "cannot open %s", path);
+    CkptHeader h;
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "YFCKPT1", 8) != 0 || h.nx != g->nx ||
+        h.ny != g->ny || h.nz != g->nz || h.prec != g->prec || h.pml_n != g->pml_n ||
+        h.nf_total != g->nf_total) {
+        fclose(fp);
+        return fail(YF_E_INVALID, "checkpoint %s does not match this grid", path);
+    }
+    bool ok = true;
+    auto load = [&](void *dev, size_t bytes) {
+        if (!ok || !dev || bytes == 0) return;
+        std::vector<char> buf(bytes);
+        ok = fread(buf.data(), 1, bytes, fp) == bytes &&
+             cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    for (int c = 0; c < 6; ++c) load(g->fld[c], g->npts * g->esz);
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 4; ++q) load(g->psi[a][q], g->psi_count[a] * g->esz);
+    load(g->acc64, (size_t)g->nf_total * 4 * sizeof(double));
+    load(g->acc32, (size_t)g->nf_total * 4 * sizeof(float));
+    load(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));
+    fclose(fp);
+    if (!ok) return fail(YF_E_INVALID, "checkpoint %s is truncated", path);
+    YF_CUDA_TRY(cudaMemcpy(g->ctr, &h.ctr, sizeof(long long), cudaMemcpyHostToDevice));
+    YF_CUDA_TRY(cudaMemcpy(g->status, &h.status, sizeof(int), cudaMemcpyHostToDevice));
+    g->steps_done = h.steps;
+    return YF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "yeefdtd.h"
+
+namespace yf {
+
+// CODATA 2018 vacuum constants (SI)
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kEps0 = 8.8541878128e-12;
+
+constexpr int kMaxClasses = 256;   // uint8 edge classes, class 0 = PEC
+constexpr int kMaxPorts = 16;
+constexpr int kEpiThreads = 512;   // block size of the per-step port epilogue
+constexpr int kEnergyBlocks = 592; // 4 x 148 SMs: fixed partial count -> fixed sum order
+
+// Records a message for yf_last_error() and returns the status.
+yf_status fail(yf_status s, const char *fmt, ...);
+yf_status cuda_fail(cudaError_t e, const char *what);
+
+#define YF_CUDA_TRY(expr)                                                     \
+    do {                                                                      \
+        cudaError_t e__ = (expr);                                             \
+        if (e__ != cudaSuccess) return ::yf::cuda_fail(e__, #expr);           \
+    } while (0)
+
+// One port as the epilogue kernel sees it.
+struct PortDev {
+    int plane, dir, j0, j1, k0, k1, kb, kt, m;
+    int nfreq;
+    int foff;          // offset of this port's frequencies in the concatenated lists
+    double vscale;     // -(dy dz) / width
+};
+
+template <typename T>
+struct Fields {
+    T *c[6];           // ex, ey, ez, hx, hy, hz
+};
+
+// CPML data the stencil kernels need, per axis a (0 = x, 1 = y, 2 = z):
+//   lo/hi  : absorbing slab present on the low / high face
+//   prof   : six profiles of length N_a + 1: b_e, a_e, 1/kappa_e at integer nodes,
+//            b_h, a_h, 1/kappa_h at half nodes (entry p is position p + 1/2)
+//   psi[q] : auxiliaries of the slab, q = 0,1 for the two E components with a
+//            derivative along a, q = 2,3 for the two H components (order below)
+//     axis x: Ey(dHz/dx), Ez(dHy/dx) | Hy(dEz/dx), Hz(dEy/dx)
+//     axis y: Ex(dHz/dy), Ez(dHx/dy) | Hx(dEz/dy), Hz(dEx/dy)
+//     axis z: Ex(dHy/dz), Ey(dHx/dz) | Hx(dEy/dz), Hy(dEx/dz)
+//   slab index of position p: p (p < n) or n + p - (N - n) (p >= N - n); length 2n+1
+//   psi layout: axis x [(k(ny+1) + j) L + s], axis y [(k L + s) px + i],
+//               axis z [(s(ny+1) + j) px + i]
+template <typename T>
+struct Pml {
+    int n;
+    int lo[3], hi[3];
+    int len;
+    const T *prof[3];
+    T *psi[3][4];
+};
+
+template <typename T>
+struct StencilParams {
+    int nx, ny, nz, px;
+    long plane;        // px * (ny + 1)
+    T rdx, rdy, rdz;   // 1 / d
+    T db;              // dt / mu0
+    const uint8_t *cls[3];
+    const T *ctab;     // [kMaxClasses][2] = (Ca, Cb)
+    Pml<T> pml;
+};
+
+template <typename T>
+struct EpiParams {
+    T *ez;                   // field buffer the source writes into and V reads
+    const T *hy, *hz;        // H^{n+1/2}
+    const uint8_t *cls_z;
+    int nx, ny, nz, px;
+    long plane;
+    // source
+    int src_kind, src_plane, sj0, sj1, sk0, sk1;
+    double amp, p0, p1, t0, dt;
+    const double *table;
+    long table_len;
+    // ports and DFT
+    int nports;
+    const PortDev *ports;
+    const unsigned long long *inc;   // per frequency: round(f dt / 2 * 2^64)
+    int dft_mask;
+    double *acc64;   // [nf_total][4]  V re, V im, I re, I im
+    float *acc32;    // [nf_total][4]
+    float *kahan;    // [nf_total][8]  (sum, compensation) x 4
+    double dy, dz;
+    long long *ctr;  // steps completed
+    int *status;     // bit 0: non-finite port sample
+};
+
+// kernel launchers (yf_kernels.cu)
+template <typename T>
+cudaError_t launch_update_h(const StencilParams<T> &p, const Fields<T> &f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_e(const StencilParams<T> &p, const Fields<T> &f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sanitize(const Fields<T> &f, uint8_t *const cls[3], int nx, int ny, int nz,
+                            int px, long plane, cudaStream_t s);
+template <typename T>
+cudaError_t launch_energy(const T *const c[6], const uint8_t *const cls[3], const double *eps_tab,
+                          int nx, int ny, int nz, int px, long plane, double *partials,
+                          double *out, cudaStream_t s);
+
+// materials (yf_materials.cu)
+struct MaterialResult {
+    int nclass;                       // including class 0
+    std::vector<double> eps_r, sigma; // per class (class 0 unused)
+};
+yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const uint8_t *ids_dev,
+                              int nmat, const double *eps_r, const double *sigma,
+                              const uint8_t *is_pec, uint8_t *cls_dev[3], MaterialResult *res,
+                              cudaStream_t s);
+yf_status apply_pec_sheet(int nx, int ny, int nz, int px, long plane, uint8_t *cls_dev[3],
+                          const int sheet[6], cudaStream_t s);
+
+}  // namespace yf

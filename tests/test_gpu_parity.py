@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+  FP64 fields      relative L2 over all six components <= 1e-12 after 2000 steps
+  FP64 port DFTs   relative (to the spectrum's max)    <= 1e-10
+  FP32 fields      relative L2                         <= 1e-5
+  FP32 |S_ij|      absolute                            <= 1e-3
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import post, yee
+from paper_2208_04371_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+@pytest.fixture(scope="module")
+def small_fp64_ref():
+    p = W.config_small_fp64()
+    return p, yee.run(p, want_fields=True)
+
+
+def test_small_microstrip_fp64_fields_and_dfts(gpu, small_fp64_ref):
+    p, ref = small_fp64_ref
+    with gpu.Grid(p, prec=gpu.FP64) as g:
+        assert g.dt == pytest.approx(ref["dt"], rel=1e-15)
+        g.step(p.nsteps)
+        g.sync()
+        f = g.fields()
+        V, I = g.port_dfts()
+    assert rel_l2(f, ref["fields"]) <= 1e-12
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    for q in range(2):
+        assert np.max(np.abs(V[q] - Vo[q])) <= 1e-10 * np.max(np.abs(Vo[q]))
+        assert np.max(np.abs(I[q] - Io[q])) <= 1e-10 * np.max(np.abs(Io[q]))
+
+
+def test_small_microstrip_fp32_within_budget(gpu, small_fp64_ref):
+    """FP32 fields: relative L2 <= 1e-5 at the pulse peak (step 1000, t = t0), and at step
+    2000 the error norm stays below 1e-5 of the run's field scale (the peak-time norm).
+    By step 2000 the pulse has left through the PML and the remaining tail is ~140x smaller
+    than the peak, so a ratio to the tail alone would measure the tail, not FP32."""
+    p, ref = small_fp64_ref
+    ref_mid = yee.run(p, nsteps=1000, want_fields=True)["fields"]
+    with gpu.Grid(p, prec=gpu.FP32) as g:
+        g.step(1000)
+        f_mid = g.fields()
+        g.step(p.nsteps - 1000)
+        g.sync()
+        f = g.fields()
+        sp = gpu.read_sparams(g.h, len(p.freqs))
+    assert rel_l2(f_mid, ref_mid) <= 1e-5
+    scale = np.linalg.norm(ref_mid.ravel())
+    assert np.linalg.norm((f - ref["fields"]).ravel()) / scale <= 1e-5
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    So, Zo = post.sstar_uniform(Vo, Io, [1, -1])
+    Sno = post.renormalize(So, Zo)
+    assert np.max(np.abs(np.abs(sp["S_star"]) - np.abs(So))) <= 1e-3
+    assert np.max(np.abs(np.abs(sp["S"]) - np.abs(Sno))) <= 1e-3
+
+
+def test_sparams_kernel_matches_oracle_postprocessing(gpu, small_fp64_ref):
+    """Uniform-line extraction on the GPU (FP64) vs the oracle's numpy route, same inputs."""
+    p, ref = small_fp64_ref
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    So, Zo = post.sstar_uniform(Vo, Io, [1, -1])
+    Sn = post.renormalize(So, Zo)
+    zc = post.zc_from_sstar(So, Zo)
+    tau = post.phase_delay(So[:, 1, 0], p.freqs)
+    r = gpu.sparams(p.freqs, np.array([Vo[0], Vo[1]]), np.array([Io[0], -Io[1]]),
+                    np.zeros((2, 2, len(p.freqs)), complex))
+    # the full-protocol call with V_tot = 0 gives S*_jj = -1; check Z_r there, then the
+    # uniform-line call through a grid for the rest
+    assert np.max(np.abs(r["Zr"] - Zo) / np.abs(Zo)) < 1e-13
+    with gpu.Grid(p, prec=gpu.FP64) as g:
+        g.step(p.nsteps)
+        u = gpu.read_sparams(g.h, len(p.freqs))
+    assert np.max(np.abs(u["S_star"] - So)) < 1e-10
+    assert np.max(np.abs(u["S"] - Sn)) < 1e-10
+    assert np.max(np.abs(u["Zc"] - zc) / np.abs(zc)) < 1e-9
+    assert np.max(np.abs(u["tau"][:, 1, 0] - tau) / np.abs(tau)) < 1e-9
+
+
+def test_full_protocol_sparams_kernel_vs_oracle(gpu):
+    """Eq. 1, 2, 5-6, 8 on synthetic three-port spectra: GPU FP64 kernel vs numpy oracle."""
+    rng = np.random.default_rng(5)
+    N, F = 3, 40
+    freqs = np.linspace(1e9, 40e9, F)
+    Vi = rng.normal(size=(N, F)) + 1j * rng.normal(size=(N, F))
+    Ii = Vi / (np.array([[30.0], [55.0], [80.0]]) + 1j * rng.normal(size=(N, F)))
+    Vt = Vi[:, None, :] * (0.3 * (rng.normal(size=(N, N, F)) + 1j * rng.normal(size=(N, N, F))))
+    So, Zo = post.sstar(Vi, Ii, Vt)
+    Sn = post.renormalize(So, Zo)
+    r = gpu.sparams(freqs, Vi, Ii, Vt)
+    assert np.max(np.abs(r["S_star"] - So)) < 1e-12 * np.max(np.abs(So))
+    assert np.max(np.abs(r["Zr"] - Zo)) < 1e-12 * np.max(np.abs(Zo))
+    assert np.max(np.abs(r["S"] - Sn)) < 1e-11 * np.max(np.abs(Sn))
+
+
+def _ragged_problem():
+    """Ragged grid (no axis a multiple of 32), PML on five faces, random lossy materials,
+    a PEC block, sheets on all three normals, a differential-Gaussian source."""
+    nx, ny, nz = 45, 37, 29
+    rng = W.SplitMix64(99)
+    ids = np.array([rng.randint(0, 4) for _ in range(nx * ny * nz)], np.uint8).reshape(nz, ny, nx)
+    ids[10:14, 15:20, 20:25] = 5
+    p = W.Problem(nx=nx, ny=ny, nz=nz, dx=4e-6, dy=5e-6, dz=3e-6, courant=0.95, ids=ids,
+                  eps_r=np.array([1.0, 2.2, 4.0, 9.8, 3.0, 1.0]),
+                  sigma=np.array([0.0, 0.5, 0.0, 20.0, 1e4, 0.0]),
+                  mu_r=np.ones(6), is_pec=np.array([0, 0, 0, 0, 0, 1], np.uint8),
+                  sheets=[(2, 9, 5, 40, 15, 22), (1, 30, 3, 20, 4, 12), (0, 35, 10, 20, 3, 9)],
+                  bc=(1, 1, 1, 1, 0, 1), pml_cells=6, pml_order=3, pml_kappa_max=3.0,
+                  pml_alpha_max=2e8)
+    p.source = W.Source(kind=W.WAVE_DIFF_GAUSS, plane=9, j0=15, j1=22, k0=0, k1=9,
+                        amplitude=2.5, param0=3e-14)
+    p.ports = [W.Port(plane=14, direction=1, j0=15, j1=22, k0=0, k1=9, kb=9, kt=9, margin=1),
+               W.Port(plane=30, direction=-1, j0=15, j1=22, k0=0, k1=9, kb=9, kt=9, margin=2)]
+    p.freqs = np.linspace(50e9, 2e12, 37)
+    p.nsteps = 600
+    return p
+
+
+def test_ragged_lossy_grid_fp64_parity(gpu):
+    p = _ragged_problem()
+    ref = yee.run(p, want_fields=True)
+    with gpu.Grid(p, prec=gpu.FP64) as g:
+        g.step(p.nsteps)
+        g.sync()
+        f = g.fields()
+        V, I = g.port_dfts()
+    assert rel_l2(f, ref["fields"]) <= 1e-12
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    assert np.max(np.abs(V - Vo)) <= 1e-10 * np.max(np.abs(Vo))
+    assert np.max(np.abs(I - Io)) <= 1e-10 * np.max(np.abs(Io))
+
+
+def test_cavity_mode_on_gpu_follows_dispersion(gpu):
+    """Exact discrete eigenmode written in through the ABI; FP64 GPU evolution matches the
+    Yee dispersion closed form to roundoff."""
+    nx, ny, nz, d = 20, 16, 12, 1e-3
+    p = W.Problem(nx=nx, ny=ny, nz=nz, dx=d, dy=d, dz=d, courant=0.9,
+                  ids=np.zeros((nz, ny, nx), np.uint8), eps_r=np.array([1.0]),
+                  sigma=np.array([0.0]), mu_r=np.array([1.0]), is_pec=np.array([0], np.uint8),
+                  bc=(0,) * 6, pml_cells=0)
+    K, J, I = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    m, n = 3, 2
+    shape = np.sin(m * math.pi * I / nx) * np.sin(n * math.pi * J / ny) * (K < nz)
+    f0 = np.zeros((6, nz + 1, ny + 1, nx + 1))
+    f0[2] = shape
+    lam = sum((2 / d * math.sin(q * math.pi / (2 * N))) ** 2 for q, N in ((m, nx), (n, ny)))
+    N = 500
+    with gpu.Grid(p, prec=gpu.FP64) as g:
+        g.set_fields(f0)
+        g.step(N)
+        out = g.fields()
+        dt = g.dt
+    c2 = 1.0 / (yee.MU0 * yee.EPS0)
+    gg = dt * dt * c2 * lam
+    th = math.acos(1 - gg / 2)
+    aN = math.cos(N * th) + (1 - gg - math.cos(th)) / math.sin(th) * math.sin(N * th)
+    assert np.max(np.abs(out[2] - aN * shape)) < 2e-12
+
+
+def test_dft_accumulator_variants_agree(gpu):
+    p = W.config_small_fp64()
+    with gpu.Grid(p, prec=gpu.FP32, dft_mask=gpu.DFT_FP64 | gpu.DFT_KAHAN32 | gpu.DFT_FP32) as g:
+        g.step(p.nsteps)
+        V64, I64 = g.port_dfts(gpu.DFT_FP64)
+        Vk, Ik = g.port_dfts(gpu.DFT_KAHAN32)
+        V32, I32 = g.port_dfts(gpu.DFT_FP32)
+    scale = np.max(np.abs(V64))
+    assert np.max(np.abs(Vk - V64)) < 1e-6 * scale
+    assert np.max(np.abs(V32 - V64)) < 1e-4 * scale
+
+
+def test_graph_chunks_equal_single_steps(gpu):
+    p = W.config_small_fp64()
+    with gpu.Grid(p, prec=gpu.FP32) as a, gpu.Grid(p, prec=gpu.FP32) as b:
+        a.step(77)
+        for _ in range(77):
+            b.step(1)
+        assert np.array_equal(a.fields(), b.fields())
+        assert gpu.steps_done(a.h) == 77
+
+
+def test_checkpoint_resume_is_bitwise(gpu):
+    p = _ragged_problem()
+    with gpu.Grid(p, prec=gpu.FP32) as a:
+        a.step(400)
+        full = a.fields()
+        Va, Ia = a.port_dfts()
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ck.bin")
+        with gpu.Grid(p, prec=gpu.FP32) as b:
+            b.step(200)
+            gpu.checkpoint_save(b.h, path)
+        with gpu.Grid(p, prec=gpu.FP32) as c:
+            gpu.checkpoint_load(c.h, path)
+            c.step(200)
+            assert np.array_equal(c.fields(), full)
+            Vc, Ic = c.port_dfts()
+    assert np.array_equal(Va, Vc) and np.array_equal(Ia, Ic)
+
+
+def test_energy_monitor_matches_definition(gpu):
+    """yf_energy on written fields equals sum eps E^2 + mu0 H^2 over live entries."""
+    p = _ragged_problem()
+    p.bc = (0,) * 6
+    f = W.random_fields((p.nz + 1, p.ny + 1, p.nx + 1), seed=4)
+    with gpu.Grid(p, prec=gpu.FP64, with_source=False, with_ports=False) as g:
+        g.set_fields(f)
+        got = gpu.energy(g.h)
+        live = g.fields()
+    # eps per E edge from the oracle's averaging rule, via an oracle run of 0 steps is not
+    # available; use the live (sanitised) fields and the edge-average rule directly
+    ids, er = p.ids, p.eps_r
+    nz, ny, nx = ids.shape
+    e = np.zeros(3)
+    w = 0.0
+    def cell(i, j, k):
+        return er[ids[k, j, i]]
+    for comp in range(3):
+        arr = live[comp]
+        ks, js, is_ = np.nonzero(arr)
+        for k, j, i in zip(ks, js, is_):
+            if comp == 0:
+                cs = [(i, j - 1, k - 1), (i, j, k - 1), (i, j - 1, k), (i, j, k)]
+            elif comp == 1:
+                cs = [(i - 1, j, k - 1), (i, j, k - 1), (i - 1, j, k), (i, j, k)]
+            else:
+                cs = [(i - 1, j - 1, k), (i, j - 1, k), (i - 1, j, k), (i, j, k)]
+            eps = sum(cell(*c) for c in cs) / 4.0 * yee.EPS0
+            w += eps * arr[k, j, i] ** 2
+    w += yee.MU0 * np.sum(live[3:] ** 2)
+    w *= p.dx * p.dy * p.dz
+    assert got == pytest.approx(w, rel=1e-12)
+
+
+def test_nonfinite_port_sample_reports_unstable(gpu):
+    p = W.config_small_fp64()
+    with gpu.Grid(p, prec=gpu.FP32) as g:
+        f = np.zeros((6, p.nz + 1, p.ny + 1, p.nx + 1))
+        f[2, 3, 16, 14] = np.inf            # on port 1's V surface
+        g.set_fields(f)
+        g.step(1)
+        with pytest.raises(gpu.YFError) as e:
+            g.sync()
+        assert e.value.code == gpu.E_UNSTABLE
+
+
+def test_state_and_argument_errors(gpu):
+    p = W.config_small_fp64()
+    with gpu.Grid(p, prec=gpu.FP32) as g:
+        with pytest.raises(gpu.YFError) as e:
+            gpu.add_port(g.h, 0, 1, 13, 19, 0, 8, 8, 8, 1, p.freqs)
+        assert e.value.code == gpu.E_INVALID
+        g.step(1)
+        with pytest.raises(gpu.YFError) as e:
+            gpu.add_port(g.h, 20, 1, 13, 19, 0, 8, 8, 8, 1, p.freqs)
+        assert e.value.code == gpu.E_STATE
+    with pytest.raises(gpu.YFError) as e:
+        bad = W.config_small_fp64()
+        bad.mu_r = np.array([1.0, 2.0])
+        gpu.Grid(bad)
+    assert e.value.code == gpu.E_UNSUPPORTED
+
+
+def _subbox_check(f0, f1, prob, box, nsteps, dt, tol):
+    """Oracle on a sub-box seeded with the GPU's state at step n0 (f0, the box's nodes) for
+    nsteps; compare the points farther than nsteps + 1 cells from every sub-box face (outside
+    the dependency cone of the box boundary) with the GPU state f1 after those steps."""
+    (x0, x1), (y0, y1), (z0, z1) = box
+    sub = W.Problem(nx=x1 - x0, ny=y1 - y0, nz=z1 - z0, dx=prob.dx, dy=prob.dy, dz=prob.dz,
+                    courant=prob.courant, ids=np.ascontiguousarray(prob.ids[z0:z1, y0:y1, x0:x1]),
+                    eps_r=prob.eps_r, sigma=prob.sigma, mu_r=prob.mu_r, is_pec=prob.is_pec,
+                    sheets=[], bc=(0,) * 6, pml_cells=0)
+    r = yee.run(sub, nsteps=nsteps, dt=dt, fields_in=np.ascontiguousarray(f0), want_fields=True)
+    m = nsteps + 2
+    got = f1[:, m:-m, m:-m, m:-m]
+    want = r["fields"][:, m:-m, m:-m, m:-m]
+    scale = np.max(np.abs(want))
+    assert scale > 0
+    err = np.max(np.abs(got - want)) / scale
+    assert err <= tol, err
+
+
+def test_full_size_lossy_line_sampled_parity(gpu):
+    """The 768x384x256 lossy line (FP32, the benchmark workload and launch configuration):
+    after 120 steps, 8 more GPU steps agree element-wise with the oracle run on a sub-box
+    seeded with the GPU state (strip, oxide layers and Si inside the box)."""
+    p = W.config_lossy_line(nsteps=0)
+    j0, j1 = p.ports[0].j0, p.ports[0].j1
+    box = ((22, 70), ((j0 + j1) // 2 - 30, (j0 + j1) // 2 + 30), (170, 226))
+    with gpu.Grid(p, prec=gpu.FP32) as g:
+        g.step(120)
+        f0 = g.fields(box)
+        g.step(8)
+        f1 = g.fields(box)
+        dt = g.dt
+    _subbox_check(f0, f1, p, box, 8, dt, 2e-5)
