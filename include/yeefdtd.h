@@ -190,6 +190,29 @@ yf_status yf_sparams(int nports, int nfreq, const double *freqs, const yf_port_d
                      const yf_port_dfts *tot, double z_ref, double *S_star, double *S, double *Zr,
                      double *Zc, double *tau);
 
+/* Same extraction as yf_sparams, for callers that cannot allocate GPU memory: code that
+ * enqueues work while a stream is being captured in global mode (where cudaMalloc is not
+ * allowed), or programs whose device memory is owned by their own pool or arena.  The paper
+ * has no counterpart; it is an interface addition of this library.
+ *   - allocates nothing: no cudaMalloc / cudaFree.  All pointers are DEVICE pointers owned by
+ *     the caller; complex values are interleaved (re, im):
+ *       freqs [F]; V_inc, I_inc [N][F]; V_tot [N][N][F] (driven j, port i);
+ *       S [F][N][N] and Zr [N][F] required; S_star [F][N][N], Zc [F] (N == 2) and
+ *       tau [F][N][N] optional (NULL skips them).
+ *   - its scratch (the S* matrix the phase-delay pass reads) is one fixed array per GPU,
+ *     held from library load until process exit: nfreq * nports^2 <= 32768 complex entries
+ *     (512 KiB); larger requests return YF_E_INVALID before any work is queued.
+ *   - asynchronous on `stream` (NULL = legacy default stream); the caller synchronises.
+ *   - the first call on each device looks up the scratch address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - every call shares the one scratch array and overwrites all of it that it uses: calls
+ *     that may overlap on the GPU (different streams, concurrent host threads) race; order
+ *     them on one stream or synchronise between them. */
+yf_status yf_sparams_noalloc(int nports, int nfreq, const double *freqs, const double *V_inc,
+                             const double *I_inc, const double *V_tot, double z_ref,
+                             double *S_star, double *S, double *Zr, double *Zc, double *tau,
+                             void *stream);
+
 /* Uniform-line shortcut for a two-port grid driven at port 0 (incident and total runs
  * coincide; S*_11 = S*_22 = 0, S*_12 = S*_21; port 1's Z_r from the same forward wave).
  * Uses the FP64 accumulators and port 0's frequency list. */

@@ -291,3 +291,85 @@ extern "C" yf_status yf_sparams(int nports, int nfreq, const double *freqs, cons
     }
     return run_sparams(n, nf, freqs, vinc, iinc, vtot, 0, 1, z_ref, S_star, S, Zr, Zc, tau);
 }
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the extraction above.  Its only scratch, the power-mode
+// matrix S* that the phase-delay pass reads back, lives in a fixed device array instead of
+// a per-call cudaMalloc, and the caller provides every input and output on the device.
+
+#include <mutex>
+
+namespace yf {
+namespace {
+
+constexpr int kNoAllocMaxEntries = 32768;   // nfreq * nports^2 complex entries (512 KiB)
+constexpr int kNoAllocMaxDevices = 64;
+
+// One copy per GPU that loads this library, kept until the process exits.  Host code must
+// not pass the symbol itself to a kernel: on the host it names a stand-in, not device
+// memory.  The device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) cplx g_noalloc_sstar[kNoAllocMaxEntries];
+
+std::mutex g_noalloc_mu;
+cplx *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Once per device, with that device current: look up the array's device address.
+yf_status noalloc_scratch(cplx **out)
+{
+    int dev = -1;
+    YF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(YF_E_UNSUPPORTED, "yf_sparams_noalloc: device %d beyond the %d supported", dev,
+                    kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sstar);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_sstar)");
+        g_noalloc_ptr[dev] = (cplx *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return YF_OK;
+}
+
+}  // namespace
+}  // namespace yf
+
+extern "C" yf_status yf_sparams_noalloc(int nports, int nfreq, const double *freqs,
+                                        const double *V_inc, const double *I_inc,
+                                        const double *V_tot, double z_ref, double *S_star,
+                                        double *S, double *Zr, double *Zc, double *tau,
+                                        void *stream)
+{
+    using namespace yf;
+    if (nports < 1 || nports > kMaxN || nfreq < 1 || !(z_ref > 0))
+        return fail(YF_E_INVALID, "yf_sparams_noalloc: need 1 <= nports <= %d, nfreq >= 1, z_ref > 0",
+                    kMaxN);
+    if (!freqs || !V_inc || !I_inc || !V_tot || !S || !Zr)
+        return fail(YF_E_INVALID, "yf_sparams_noalloc: freqs, V_inc, I_inc, V_tot, S and Zr are required");
+    const long entries = (long)nfreq * nports * nports;
+    if (entries > kNoAllocMaxEntries)
+        return fail(YF_E_INVALID,
+                    "yf_sparams_noalloc: nfreq * nports^2 = %ld exceeds the fixed scratch of %d entries",
+                    entries, kNoAllocMaxEntries);
+    cplx *scratch = nullptr;
+    yf_status st = noalloc_scratch(&scratch);
+    if (st != YF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    SpArgs A;
+    A.n = nports; A.nf = nfreq; A.uniform = 0; A.dir1 = 1; A.z_ref = z_ref;
+    A.vinc = (const cplx *)V_inc;
+    A.iinc = (const cplx *)I_inc;
+    A.vtot = (const cplx *)V_tot;
+    A.sstar = scratch;            // fully rewritten by every call: nothing to clear
+    A.s = (cplx *)S;
+    A.zr = (cplx *)Zr;
+    A.zc = (nports == 2) ? (cplx *)Zc : nullptr;
+    k_sparams<<<(nfreq + 63) / 64, 64, 0, s>>>(A);
+    if (tau) k_phase_delay<<<1, 64, 0, s>>>(scratch, freqs, nports, nfreq, tau);
+    YF_CUDA_TRY(cudaGetLastError());
+    if (S_star)
+        YF_CUDA_TRY(cudaMemcpyAsync(S_star, scratch, (size_t)entries * sizeof(cplx),
+                                    cudaMemcpyDeviceToDevice, s));
+    return YF_OK;
+}

@@ -85,6 +85,7 @@ _SIGS = {
     "yf_sparams": (_i, [_i, _i, _dp, C.POINTER(PortDfts), C.POINTER(PortDfts), _d, _dp, _dp,
                         _dp, _dp, _dp]),
     "yf_read_sparams": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _dp]),
+    "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
     "yf_profile_steps": (_i, [_vp, C.c_long, _dp, C.POINTER(_i)]),
     "yf_kernel_name": (C.c_char_p, [_vp, _i]),
@@ -281,6 +282,18 @@ def sparams(freqs, V_inc, I_inc, V_tot, z_ref=50.0):
                            tau.ctypes.data_as(_dp)))
     return dict(S_star=_as_complex(ss), S=_as_complex(s), Zr=_as_complex(zr),
                 Zc=_as_complex(zc) if N == 2 else None, tau=tau)
+
+
+def sparams_noalloc(nports, nfreq, freqs, V_inc, I_inc, V_tot, S, Zr, S_star=None, Zc=None,
+                    tau=None, z_ref=50.0, stream=None):
+    """Allocation-free extraction: every argument is a CUDA tensor owned by the caller
+    (float64; complex values interleaved as a trailing dimension of 2).  Asynchronous on
+    `stream` (a cudaStream_t handle, or None for the legacy default stream)."""
+    def ptr(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+    _check(_lib.yf_sparams_noalloc(nports, nfreq, ptr(freqs), ptr(V_inc), ptr(I_inc), ptr(V_tot),
+                                   z_ref, ptr(S_star), ptr(S), ptr(Zr), ptr(Zc), ptr(tau),
+                                   C.c_void_p(int(stream)) if stream else None))
 
 
 def read_sparams(g, nfreq, z_ref=50.0):
