@@ -151,6 +151,19 @@ yf_status yf_add_port(yf_grid *g, const yf_port_desc *d, int nfreq, const double
 /* Which DFT accumulators run (mask of YF_DFT_*; default YF_DFT_FP64).  Before the first step. */
 yf_status yf_set_dft_mode(yf_grid *g, int mask);
 
+/* Kernel variant of the time step (default 2):
+ *   0  reference form: one H kernel and one E kernel, updating the fields in place;
+ *   1  fused: H and E of a step in one pass (2.5-D z-march over 32 x tile_y node columns,
+ *      kseg z-planes per block), reading one field buffer and writing the other, planes
+ *      staged in shared memory by ordinary loads;
+ *   2  as 1, with the planes staged by TMA (cp.async.bulk.tensor) three planes ahead of the
+ *      computation; a bounded wait that expires makes yf_sync return YF_E_TIMEOUT;
+ *   3  as 2, skewed by one plane (H on plane t and E on plane t-1 per iteration, one block
+ *      barrier per plane, CPML auxiliaries fetched ahead of the arithmetic).
+ * tile_y in {4, 8, 16}, kseg >= 1.  All variants compute the same update; results agree to
+ * rounding.  Drops captured graphs; may be called between steps. */
+yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg);
+
 /* Advance n time steps asynchronously on the handle's stream (Sec. II-A time loop:
  * H half step, E half step, source, port sampling, DFT accumulation).  Steps are
  * replayed from captured CUDA graphs in chunks. */

@@ -1,6 +1,7 @@
 // C ABI of the single-grid solver: handle life cycle, set-up, time stepping with captured
 // CUDA graphs, read-out and checkpoints.  See include/yeefdtd.h for the contract.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -138,18 +139,74 @@ static yf_status build_pml(yf_grid *g)
         else if (a == 1) cnt = (size_t)(g->nz + 1) * L * g->px;
         else cnt = (size_t)L * (g->ny + 1) * g->px;
         g->psi_count[a] = cnt;
-        for (int q = 0; q < 4; ++q) {
-            YF_CUDA_TRY(cudaMalloc(&g->psi[a][q], cnt * g->esz));
-            YF_CUDA_TRY(cudaMemset(g->psi[a][q], 0, cnt * g->esz));
+        void **slots[6] = {&g->psiE[a][0], &g->psiE[a][1], &g->psiH[0][a][0], &g->psiH[0][a][1],
+                           &g->psiH[1][a][0], &g->psiH[1][a][1]};
+        for (int q = 0; q < 6; ++q) {
+            YF_CUDA_TRY(cudaMalloc(slots[q], cnt * g->esz));
+            YF_CUDA_TRY(cudaMemset(*slots[q], 0, cnt * g->esz));
         }
     }
     return YF_OK;
 }
 
-template <typename T>
-static void fill_params(yf_grid *g)
+// tensor maps of the TMA-staged step, for the grid's current tile height
+static yf_status encode_maps(yf_grid *g)
 {
-    StencilParams<T> &P = *reinterpret_cast<StencilParams<T> *>(g->sp);
+    if (g->tmap_tile_y == g->tile_y) return YF_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(YF_E_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int esz = (int)g->esz;
+    const int bx = esz == 4 ? tma_box_x<float>(32) : tma_box_x<double>(32);
+    const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
+    const cuuint64_t gstr[3] = {(cuuint64_t)g->px * esz, (cuuint64_t)g->plane * esz,
+                                (cuuint64_t)g->npts * esz};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)(g->tile_y + 2), 1, 3};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = encode(&g->tmF[b], esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                            4, g->buf[b], gdim, gstr, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding the field tensor map failed (%d)", (int)r);
+    }
+    const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
+    const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
+    const cuuint32_t cbox[4] = {32, (cuuint32_t)g->tile_y, 1, 3};
+    CUresult r = encode(&g->tmC, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding the class tensor map failed (%d)", (int)r);
+    YF_CUDA_TRY(tma_prepare());
+    YF_CUDA_TRY(skew_prepare());
+    if (!g->side.stream) {
+        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
+    }
+    g->tmap_tile_y = g->tile_y;
+    return YF_OK;
+}
+
+template <typename T>
+static Fields<T> fields_of(const yf_grid *g, int b)
+{
+    Fields<T> F;
+    for (int c = 0; c < 6; ++c) F.c[c] = (T *)((char *)g->buf[b] + (size_t)c * g->npts * g->esz);
+    return F;
+}
+
+template <typename T>
+static StencilParams<T> stencil_params(const yf_grid *g)
+{
+    StencilParams<T> P;
     P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.px = g->px; P.plane = g->plane;
     P.rdx = (T)(1.0 / g->dx); P.rdy = (T)(1.0 / g->dy); P.rdz = (T)(1.0 / g->dz);
     P.db = (T)(g->dt / kMu0);
@@ -161,13 +218,48 @@ static void fill_params(yf_grid *g)
         P.pml.lo[a] = g->pml_lo[a];
         P.pml.hi[a] = g->pml_hi[a];
         P.pml.prof[a] = (const T *)g->prof[a];
-        for (int q = 0; q < 4; ++q) P.pml.psi[a][q] = (T *)g->psi[a][q];
+        P.pml.psi[a][0] = (T *)g->psiE[a][0];
+        P.pml.psi[a][1] = (T *)g->psiE[a][1];
+        P.pml.psi[a][2] = (T *)g->psiH[g->hpar][a][0];
+        P.pml.psi[a][3] = (T *)g->psiH[g->hpar][a][1];
     }
-    Fields<T> &F = *reinterpret_cast<Fields<T> *>(g->fp);
-    for (int c = 0; c < 6; ++c) F.c[c] = (T *)g->fld[c];
+    return P;
+}
 
-    EpiParams<T> &E = *reinterpret_cast<EpiParams<T> *>(g->ep);
-    E.ez = (T *)g->fld[2]; E.hy = (const T *)g->fld[4]; E.hz = (const T *)g->fld[5];
+template <typename T>
+static FusedArgs<T> fused_args(const yf_grid *g)
+{
+    FusedArgs<T> F;
+    F.nx = g->nx; F.ny = g->ny; F.nz = g->nz; F.px = g->px; F.kseg = g->kseg;
+    F.tx0 = 0; F.ty0 = 0; F.z0 = 0; F.z1 = g->nz;
+    F.plane = g->plane; F.npts = g->npts;
+    F.rdx = (T)(1.0 / g->dx); F.rdy = (T)(1.0 / g->dy); F.rdz = (T)(1.0 / g->dz);
+    F.db = (T)(g->dt / kMu0);
+    for (int c = 0; c < 3; ++c) F.cls[c] = g->cls[c];
+    F.ctab = (const T *)g->ctab;
+    F.A = (const T *)g->buf[g->cur];
+    F.B = (T *)g->buf[g->cur ^ 1];
+    F.n = g->pml_n;
+    F.L = 2 * g->pml_n + 1;
+    for (int a = 0; a < 3; ++a) {
+        F.lo[a] = g->pml_lo[a];
+        F.hi[a] = g->pml_hi[a];
+        F.prof[a] = (const T *)g->prof[a];
+        for (int q = 0; q < 2; ++q) {
+            F.psiE[a][q] = (T *)g->psiE[a][q];
+            F.psiHr[a][q] = (const T *)g->psiH[g->hpar][a][q];
+            F.psiHw[a][q] = (T *)g->psiH[g->hpar ^ 1][a][q];
+        }
+    }
+    return F;
+}
+
+template <typename T>
+static EpiParams<T> epi_params(const yf_grid *g)
+{
+    EpiParams<T> E;
+    E.segs = g->segs_dev; E.nseg = (int)g->segs.size(); E.slots = g->slots; E.ticket = g->ticket;
+    E.ez = (T *)g->fld(2); E.hy = (const T *)g->fld(4); E.hz = (const T *)g->fld(5);
     E.cls_z = g->cls[2];
     E.nx = g->nx; E.ny = g->ny; E.nz = g->nz; E.px = g->px; E.plane = g->plane;
     E.src_kind = g->has_src ? g->src.kind : YF_WAVE_NONE;
@@ -179,6 +271,24 @@ static void fill_params(yf_grid *g)
     E.acc64 = g->acc64; E.acc32 = g->acc32; E.kahan = g->kahan;
     E.dy = g->dy; E.dz = g->dz;
     E.ctr = g->ctr; E.status = g->status;
+    return E;
+}
+
+// epilogue work items: source rectangle, each port's V surface and I loops
+static void build_segments(yf_grid *g)
+{
+    g->segs.clear();
+    auto add = [&](int kind, int port, int total) {
+        for (int s = 0; s < total; s += kEpiSegPoints)
+            g->segs.push_back({kind, port, s, total - s < kEpiSegPoints ? total - s : kEpiSegPoints});
+    };
+    if (g->has_src) add(0, -1, (g->sj1 - g->sj0 + 1) * (g->sk1 - g->sk0));
+    for (int p = 0; p < (int)g->ports.size(); ++p) {
+        const PortDev &d = g->ports[p];
+        add(1, p, (d.j1 - d.j0 + 1) * (d.k1 - d.k0));
+        const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
+        add(2, p, 2 * (2 * nyl + 2 * nzl));
+    }
 }
 
 yf_status finalize(yf_grid *g)
@@ -222,8 +332,22 @@ yf_status finalize(yf_grid *g)
                                g->src_table_host.size() * sizeof(double), cudaMemcpyHostToDevice));
         g->src_table_len = (long)g->src_table_host.size();
     }
-    if (g->prec == YF_FP32) fill_params<float>(g);
-    else fill_params<double>(g);
+    for (const PortDev &d : g->ports)
+        if (g->has_src && d.plane == g->src_plane)
+            return fail(YF_E_INVALID, "a port may not sit on the source plane x = %d", d.plane);
+    build_segments(g);
+    const int nseg = (int)g->segs.size();
+    if (nseg > 0) {
+        YF_CUDA_TRY(cudaMalloc(&g->segs_dev, nseg * sizeof(EpiSeg)));
+        YF_CUDA_TRY(cudaMemcpy(g->segs_dev, g->segs.data(), nseg * sizeof(EpiSeg), cudaMemcpyHostToDevice));
+        YF_CUDA_TRY(cudaMalloc(&g->slots, nseg * sizeof(double)));
+    }
+    YF_CUDA_TRY(cudaMalloc(&g->ticket, sizeof(unsigned int)));
+    YF_CUDA_TRY(cudaMemset(g->ticket, 0, sizeof(unsigned int)));
+    if (g->variant >= 2) {
+        st = encode_maps(g);
+        if (st != YF_OK) return st;
+    }
     g->started = true;
     return YF_OK;
 }
@@ -231,14 +355,26 @@ yf_status finalize(yf_grid *g)
 template <typename T>
 static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
 {
-    const StencilParams<T> &P = *reinterpret_cast<const StencilParams<T> *>(g->sp);
-    const Fields<T> &F = *reinterpret_cast<const Fields<T> *>(g->fp);
-    const EpiParams<T> &E = *reinterpret_cast<const EpiParams<T> *>(g->ep);
-    cudaError_t e = launch_update_h<T>(P, F, s);
-    if (e != cudaSuccess) return e;
-    e = launch_update_e<T>(P, F, s);
-    if (e != cudaSuccess) return e;
-    return launch_epilogue<T>(E, s);
+    cudaError_t e;
+    if (g->variant >= 1) {
+        if (g->variant == 3)
+            e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, s);
+        else if (g->variant == 2)
+            e = launch_tma<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, s, &g->side);
+        else
+            e = launch_fused<T>(fused_args<T>(g), g->tile_y, s);
+        if (e != cudaSuccess) return e;
+        g->cur ^= 1;
+        g->hpar ^= 1;
+    } else {
+        const StencilParams<T> P = stencil_params<T>(g);
+        const Fields<T> F = fields_of<T>(g, g->cur);
+        e = launch_update_h<T>(P, F, s);
+        if (e != cudaSuccess) return e;
+        e = launch_update_e<T>(P, F, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_epilogue<T>(epi_params<T>(g), s);
 }
 
 static cudaError_t step_direct(yf_grid *g, cudaStream_t s)
@@ -255,9 +391,9 @@ static yf_status capture_chunk(yf_grid *g)
     cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
     if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing step chunk"); }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    e = cudaGraphInstantiate(&g->graph[g->cur], graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    if (e != cudaSuccess) { g->graph[g->cur] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
     return YF_OK;
 }
 
@@ -306,14 +442,14 @@ yf_status yf_grid_create(int nx, int ny, int nz, double dx, double dy, double dz
     }
     auto bail = [&](cudaError_t e, const char *w) { yf_status s = cuda_fail(e, w); yf_grid_destroy(g); return s; };
     cudaError_t e;
-    for (int c = 0; c < 6; ++c) {
-        if ((e = cudaMalloc(&g->fld[c], g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc fields");
-        if ((e = cudaMemset(g->fld[c], 0, g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMemset fields");
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&g->buf[b], 6 * g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc fields");
+        if ((e = cudaMemset(g->buf[b], 0, 6 * g->npts * g->esz)) != cudaSuccess) return bail(e, "cudaMemset fields");
     }
-    for (int c = 0; c < 3; ++c) {
-        if ((e = cudaMalloc(&g->cls[c], g->npts)) != cudaSuccess) return bail(e, "cudaMalloc classes");
-        if ((e = cudaMemset(g->cls[c], 0, g->npts)) != cudaSuccess) return bail(e, "cudaMemset classes");
-    }
+    g->tile_y = prec == YF_FP32 ? 8 : 8;
+    if ((e = cudaMalloc(&g->cls_base, 3 * g->npts)) != cudaSuccess) return bail(e, "cudaMalloc classes");
+    if ((e = cudaMemset(g->cls_base, 0, 3 * g->npts)) != cudaSuccess) return bail(e, "cudaMemset classes");
+    for (int c = 0; c < 3; ++c) g->cls[c] = g->cls_base + c * g->npts;
     if ((e = cudaMalloc(&g->ctab, 2 * kMaxClasses * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc ctab");
     if ((e = cudaMalloc(&g->eps_tab, kMaxClasses * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc eps");
     if ((e = cudaMalloc(&g->ctr, sizeof(long long))) != cudaSuccess) return bail(e, "cudaMalloc ctr");
@@ -331,12 +467,24 @@ yf_status yf_grid_destroy(yf_grid *g)
 {
     if (!g) return YF_OK;
     if (g->stream) cudaStreamSynchronize(g->stream);
-    if (g->graph) cudaGraphExecDestroy(g->graph);
-    for (int c = 0; c < 6; ++c) cudaFree(g->fld[c]);
-    for (int c = 0; c < 3; ++c) cudaFree(g->cls[c]);
+    for (int b = 0; b < 2; ++b)
+        if (g->graph[b]) cudaGraphExecDestroy(g->graph[b]);
+    for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
+    cudaFree(g->cls_base);
     for (int a = 0; a < 3; ++a) {
         cudaFree(g->prof[a]);
-        for (int q = 0; q < 4; ++q) cudaFree(g->psi[a][q]);
+        for (int q = 0; q < 2; ++q) {
+            cudaFree(g->psiE[a][q]);
+            cudaFree(g->psiH[0][a][q]);
+            cudaFree(g->psiH[1][a][q]);
+        }
+    }
+    cudaFree(g->segs_dev); cudaFree(g->slots); cudaFree(g->ticket);
+    if (g->side.stream) {
+        cudaStreamSynchronize(g->side.stream);
+        cudaEventDestroy(g->side.fork);
+        cudaEventDestroy(g->side.join);
+        cudaStreamDestroy(g->side.stream);
     }
     cudaFree(g->ctab); cudaFree(g->eps_tab); cudaFree(g->ctr); cudaFree(g->status);
     cudaFree(g->energy_partials); cudaFree(g->ports_dev); cudaFree(g->inc_dev);
@@ -506,11 +654,13 @@ yf_status yf_step(yf_grid *g, long n)
     YF_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
     long done = 0;
     if (cs == cudaStreamCaptureStatusNone && n >= g->chunk) {
-        if (!g->graph) {
+        // a chunk has an even number of steps, so the buffer parity is the same before and
+        // after every replay
+        if (!g->graph[g->cur]) {
             st = capture_chunk(g);
             if (st != YF_OK) return st;
         }
-        for (; done + g->chunk <= n; done += g->chunk) YF_CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+        for (; done + g->chunk <= n; done += g->chunk) YF_CUDA_TRY(cudaGraphLaunch(g->graph[g->cur], g->stream));
     }
     for (; done < n; ++done) YF_CUDA_TRY(step_direct(g, g->stream));
     g->steps_done += n;
@@ -523,6 +673,8 @@ yf_status yf_sync(yf_grid *g)
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     int st = 0;
     YF_CUDA_TRY(cudaMemcpy(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 4) return fail(YF_E_CUDA, "TMA-staged step: shared memory base not 128-byte aligned");
+    if (st & 2) return fail(YF_E_TIMEOUT, "a bounded device wait of the TMA-staged step gave up");
     if (st & 1) return fail(YF_E_UNSTABLE, "a port sample became non-finite");
     return YF_OK;
 }
@@ -538,7 +690,7 @@ yf_status yf_read_fields(yf_grid *g, int comp, void *dst, yf_mem where)
 {
     if (!g || !dst || comp < 0 || comp > 5) return fail(YF_E_INVALID, "yf_read_fields: bad argument");
     const size_t w = (size_t)(g->nx + 1) * g->esz;
-    YF_CUDA_TRY(cudaMemcpy2DAsync(dst, w, g->fld[comp], (size_t)g->px * g->esz, w,
+    YF_CUDA_TRY(cudaMemcpy2DAsync(dst, w, g->fld(comp), (size_t)g->px * g->esz, w,
                                   (size_t)(g->ny + 1) * (g->nz + 1),
                                   where == YF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                                   g->stream));
@@ -562,20 +714,17 @@ yf_status yf_write_fields(yf_grid *g, int comp, const void *src, yf_mem where)
         if (st != YF_OK) return st;
     }
     const size_t w = (size_t)(g->nx + 1) * g->esz;
-    YF_CUDA_TRY(cudaMemcpy2DAsync(g->fld[comp], (size_t)g->px * g->esz, src, w, w,
+    YF_CUDA_TRY(cudaMemcpy2DAsync(g->fld(comp), (size_t)g->px * g->esz, src, w, w,
                                   (size_t)(g->ny + 1) * (g->nz + 1),
                                   where == YF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                   g->stream));
     cudaError_t e;
-    if (g->prec == YF_FP32) {
-        Fields<float> F;
-        for (int c = 0; c < 6; ++c) F.c[c] = (float *)g->fld[c];
-        e = launch_sanitize<float>(F, g->cls, g->nx, g->ny, g->nz, g->px, g->plane, g->stream);
-    } else {
-        Fields<double> F;
-        for (int c = 0; c < 6; ++c) F.c[c] = (double *)g->fld[c];
-        e = launch_sanitize<double>(F, g->cls, g->nx, g->ny, g->nz, g->px, g->plane, g->stream);
-    }
+    if (g->prec == YF_FP32)
+        e = launch_sanitize<float>(fields_of<float>(g, g->cur), g->cls, g->nx, g->ny, g->nz, g->px,
+                                   g->plane, g->stream);
+    else
+        e = launch_sanitize<double>(fields_of<double>(g, g->cur), g->cls, g->nx, g->ny, g->nz, g->px,
+                                    g->plane, g->stream);
     YF_CUDA_TRY(e);
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     return YF_OK;
@@ -589,12 +738,12 @@ yf_status yf_energy(yf_grid *g, double *w)
     cudaError_t e;
     if (g->prec == YF_FP32) {
         const float *c[6];
-        for (int q = 0; q < 6; ++q) c[q] = (const float *)g->fld[q];
+        for (int q = 0; q < 6; ++q) c[q] = (const float *)g->fld(q);
         e = launch_energy<float>(c, g->cls, g->eps_tab, g->nx, g->ny, g->nz, g->px, g->plane,
                                  g->energy_partials, out, g->stream);
     } else {
         const double *c[6];
-        for (int q = 0; q < 6; ++q) c[q] = (const double *)g->fld[q];
+        for (int q = 0; q < 6; ++q) c[q] = (const double *)g->fld(q);
         e = launch_energy<double>(c, g->cls, g->eps_tab, g->nx, g->ny, g->nz, g->px, g->plane,
                                   g->energy_partials, out, g->stream);
     }
@@ -666,10 +815,13 @@ yf_status yf_reset(yf_grid *g)
 {
     if (!g) return fail(YF_E_INVALID, "yf_reset: NULL grid");
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (int c = 0; c < 6; ++c) YF_CUDA_TRY(cudaMemsetAsync(g->fld[c], 0, g->npts * g->esz, g->stream));
+    for (int b = 0; b < 2; ++b) YF_CUDA_TRY(cudaMemsetAsync(g->buf[b], 0, 6 * g->npts * g->esz, g->stream));
     for (int a = 0; a < 3; ++a)
-        for (int q = 0; q < 4; ++q)
-            if (g->psi[a][q]) YF_CUDA_TRY(cudaMemsetAsync(g->psi[a][q], 0, g->psi_count[a] * g->esz, g->stream));
+        for (int q = 0; q < 2; ++q) {
+            void *ps[3] = {g->psiE[a][q], g->psiH[0][a][q], g->psiH[1][a][q]};
+            for (void *p : ps)
+                if (p) YF_CUDA_TRY(cudaMemsetAsync(p, 0, g->psi_count[a] * g->esz, g->stream));
+        }
     if (g->nf_total > 0) {
         YF_CUDA_TRY(cudaMemsetAsync(g->acc64, 0, (size_t)g->nf_total * 4 * sizeof(double), g->stream));
         YF_CUDA_TRY(cudaMemsetAsync(g->acc32, 0, (size_t)g->nf_total * 4 * sizeof(float), g->stream));
@@ -684,44 +836,59 @@ yf_status yf_reset(yf_grid *g)
     return YF_OK;
 }
 
-yf_status yf_profile_steps(yf_grid *g, long n, double *ms, int *nkern)
+}  // extern "C"
+
+template <typename T>
+static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
+{
+    cudaError_t e;
+    cudaEventRecord(ev[0], g->stream);
+    if (g->variant >= 1) {
+        if (g->variant == 3)
+            e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream);
+        else if (g->variant == 2)
+            e = launch_tma<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream, &g->side);
+        else
+            e = launch_fused<T>(fused_args<T>(g), g->tile_y, g->stream);
+        if (e != cudaSuccess) return e;
+        g->cur ^= 1;
+        g->hpar ^= 1;
+        cudaEventRecord(ev[1], g->stream);
+        *nk = 2;
+    } else {
+        const StencilParams<T> P = stencil_params<T>(g);
+        const Fields<T> F = fields_of<T>(g, g->cur);
+        if ((e = launch_update_h<T>(P, F, g->stream)) != cudaSuccess) return e;
+        cudaEventRecord(ev[1], g->stream);
+        if ((e = launch_update_e<T>(P, F, g->stream)) != cudaSuccess) return e;
+        cudaEventRecord(ev[2], g->stream);
+        *nk = 3;
+    }
+    e = launch_epilogue<T>(epi_params<T>(g), g->stream);
+    cudaEventRecord(ev[*nk], g->stream);
+    return e;
+}
+
+extern "C" yf_status yf_profile_steps(yf_grid *g, long n, double *ms, int *nkern)
 {
     if (!g || !ms || !nkern || n < 1) return fail(YF_E_INVALID, "yf_profile_steps: bad argument");
     yf_status st = finalize(g);
     if (st != YF_OK) return st;
-    const int nk = 3;
-    cudaEvent_t ev[nk + 1];
-    for (int q = 0; q <= nk; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
-    double acc[nk] = {0, 0, 0};
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
+    double acc[3] = {0, 0, 0};
+    int nk = 0;
     cudaError_t e = cudaSuccess;
     for (long t = 0; t < n && e == cudaSuccess; ++t) {
-        cudaEventRecord(ev[0], g->stream);
-        if (g->prec == YF_FP32) {
-            const auto &P = *reinterpret_cast<const StencilParams<float> *>(g->sp);
-            const auto &F = *reinterpret_cast<const Fields<float> *>(g->fp);
-            launch_update_h<float>(P, F, g->stream);
-            cudaEventRecord(ev[1], g->stream);
-            launch_update_e<float>(P, F, g->stream);
-            cudaEventRecord(ev[2], g->stream);
-            launch_epilogue<float>(*reinterpret_cast<const EpiParams<float> *>(g->ep), g->stream);
-        } else {
-            const auto &P = *reinterpret_cast<const StencilParams<double> *>(g->sp);
-            const auto &F = *reinterpret_cast<const Fields<double> *>(g->fp);
-            launch_update_h<double>(P, F, g->stream);
-            cudaEventRecord(ev[1], g->stream);
-            launch_update_e<double>(P, F, g->stream);
-            cudaEventRecord(ev[2], g->stream);
-            launch_epilogue<double>(*reinterpret_cast<const EpiParams<double> *>(g->ep), g->stream);
-        }
-        cudaEventRecord(ev[3], g->stream);
-        e = cudaEventSynchronize(ev[3]);
+        e = g->prec == YF_FP32 ? profile_one<float>(g, ev, &nk) : profile_one<double>(g, ev, &nk);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[nk]);
         for (int q = 0; q < nk && e == cudaSuccess; ++q) {
             float m = 0.f;
             e = cudaEventElapsedTime(&m, ev[q], ev[q + 1]);
             acc[q] += m;
         }
     }
-    for (int q = 0; q <= nk; ++q) cudaEventDestroy(ev[q]);
+    for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
     YF_CUDA_TRY(e);
     g->steps_done += n;
     for (int q = 0; q < nk; ++q) ms[q] = acc[q] / (double)n;
@@ -729,11 +896,35 @@ yf_status yf_profile_steps(yf_grid *g, long n, double *ms, int *nkern)
     return YF_OK;
 }
 
+extern "C" {
+
 const char *yf_kernel_name(yf_grid *g, int idx)
 {
-    (void)g;
-    static const char *names[] = {"k_update_h", "k_update_e", "k_epilogue"};
-    return (idx >= 0 && idx < 3) ? names[idx] : "";
+    static const char *ref[] = {"k_update_h", "k_update_e", "k_epilogue"};
+    static const char *fused[] = {"k_yee_fused", "k_epilogue"};
+    static const char *tma[] = {"k_yee_tma", "k_epilogue"};
+    static const char *skew[] = {"k_yee_skew", "k_epilogue"};
+    if (!g) return "";
+    if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
+    if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
+    if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";
+    return (idx >= 0 && idx < 3) ? ref[idx] : "";
+}
+
+yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_set_variant: NULL grid");
+    if (variant < 0 || variant > 3) return fail(YF_E_INVALID, "yf_set_variant: variant must be 0..3");
+    if (tile_y != 4 && tile_y != 8 && tile_y != 16) return fail(YF_E_INVALID, "yf_set_variant: tile_y must be 4, 8 or 16");
+    if (kseg < 1) return fail(YF_E_INVALID, "yf_set_variant: kseg must be >= 1");
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int b = 0; b < 2; ++b)
+        if (g->graph[b]) { cudaGraphExecDestroy(g->graph[b]); g->graph[b] = nullptr; }
+    g->variant = variant;
+    g->tile_y = tile_y;
+    g->kseg = kseg;
+    if (g->started && variant >= 2) return encode_maps(g);
+    return YF_OK;
 }
 
 // checkpoint: header, fields, CPML auxiliaries, accumulators, counters
@@ -767,9 +958,12 @@ yf_status yf_checkpoint_save(yf_grid *g, const char *path)
         ok = cudaMemcpy(buf.data(), dev, bytes, cudaMemcpyDeviceToHost) == cudaSuccess &&
              fwrite(buf.data(), 1, bytes, fp) == bytes;
     };
-    for (int c = 0; c < 6; ++c) dump(g->fld[c], g->npts * g->esz);
+    dump(g->buf[g->cur], 6 * g->npts * g->esz);
     for (int a = 0; a < 3; ++a)
-        for (int q = 0; q < 4; ++q) dump(g->psi[a][q], g->psi_count[a] * g->esz);
+        for (int q = 0; q < 2; ++q) {
+            dump(g->psiE[a][q], g->psi_count[a] * g->esz);
+            dump(g->psiH[g->hpar][a][q], g->psi_count[a] * g->esz);
+        }
     dump(g->acc64, (size_t)g->nf_total * 4 * sizeof(double));
     dump(g->acc32, (size_t)g->nf_total * 4 * sizeof(float));
     dump(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));
@@ -800,9 +994,12 @@ yf_status yf_checkpoint_load(yf_grid *g, const char *path)
         ok = fread(buf.data(), 1, bytes, fp) == bytes &&
              cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
     };
-    for (int c = 0; c < 6; ++c) load(g->fld[c], g->npts * g->esz);
+    load(g->buf[g->cur], 6 * g->npts * g->esz);
     for (int a = 0; a < 3; ++a)
-        for (int q = 0; q < 4; ++q) load(g->psi[a][q], g->psi_count[a] * g->esz);
+        for (int q = 0; q < 2; ++q) {
+            load(g->psiE[a][q], g->psi_count[a] * g->esz);
+            load(g->psiH[g->hpar][a][q], g->psi_count[a] * g->esz);
+        }
     load(g->acc64, (size_t)g->nf_total * 4 * sizeof(double));
     load(g->acc32, (size_t)g->nf_total * 4 * sizeof(float));
     load(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));

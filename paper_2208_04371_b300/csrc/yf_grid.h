@@ -18,7 +18,12 @@ struct yf_grid {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
 
-    void *fld[6] = {};            // ex, ey, ez, hx, hy, hz
+    // two field buffers, each ex, ey, ez, hx, hy, hz at stride npts; buf[cur] is current.
+    // The fused step reads buf[cur] and writes buf[cur ^ 1]; the reference kernels update
+    // buf[cur] in place.
+    void *buf[2] = {};
+    int cur = 0;
+    void *fld(int c) const { return (char *)buf[cur] + (size_t)c * npts * esz; }
     uint8_t *cls[3] = {};         // per-edge material class of ex, ey, ez (0 = PEC)
     void *ctab = nullptr;         // [256][2] (Ca, Cb) in field precision
     double *eps_tab = nullptr;    // [256] eps0 eps_r per class
@@ -31,7 +36,11 @@ struct yf_grid {
     double pml_sigma_scale = 1.0, pml_kappa_max = 1.0, pml_alpha_max = 0.0;
     int pml_lo[3] = {}, pml_hi[3] = {};
     void *prof[3] = {};
-    void *psi[3][4] = {};
+    // CPML auxiliaries per axis: psiE[a][0..1] (E, updated in place) and two copies of the
+    // H ones, psiH[par][a][0..1]; psiH[hpar] is current (see Pml in yf_internal.h for order)
+    void *psiE[3][2] = {};
+    void *psiH[2][3][2] = {};
+    int hpar = 0;
     size_t psi_count[3] = {};
 
     bool has_src = false;
@@ -50,6 +59,10 @@ struct yf_grid {
     double *acc64 = nullptr;
     float *acc32 = nullptr, *kahan = nullptr;
     int dft_mask = YF_DFT_FP64;
+    std::vector<yf::EpiSeg> segs;
+    yf::EpiSeg *segs_dev = nullptr;
+    double *slots = nullptr;
+    unsigned int *ticket = nullptr;
 
     long long *ctr = nullptr;     // device: steps completed
     int *status = nullptr;        // device: error bits
@@ -58,13 +71,16 @@ struct yf_grid {
 
     bool started = false;
     bool geometry_open = false;   // after yf_reset: materials and sheets may change
-    int chunk = 32;               // steps per captured graph
-    cudaGraphExec_t graph = nullptr;
-
-    // kernel parameter blocks, typed by precision at finalize
-    alignas(16) unsigned char sp[sizeof(yf::StencilParams<double>)];
-    alignas(16) unsigned char fp[sizeof(yf::Fields<double>)];
-    alignas(16) unsigned char ep[sizeof(yf::EpiParams<double>)];
+    int variant = 2;              // 0: reference H and E, 1: fused step, 2: fused + TMA
+    uint8_t *cls_base = nullptr;  // the three class arrays, contiguous
+    CUtensorMap tmF[2];           // field buffers as 4-D tensors (variant 2)
+    CUtensorMap tmC;              // edge classes as a 4-D tensor
+    int tmap_tile_y = 0;          // tile the maps were encoded for (0: not encoded)
+    yf::SideStream side = {};     // frame launches of variant 2 overlap the interior
+    int tile_y = 8;               // fused: block rows (block is 32 x tile_y)
+    int kseg = 16;                // fused: z-planes per block
+    int chunk = 32;               // steps per captured graph (even)
+    cudaGraphExec_t graph[2] = {};   // one per starting buffer parity
 };
 
 namespace yf {

@@ -1,6 +1,7 @@
 // Internal types shared by the library's translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -18,7 +19,8 @@ constexpr double kEps0 = 8.8541878128e-12;
 
 constexpr int kMaxClasses = 256;   // uint8 edge classes, class 0 = PEC
 constexpr int kMaxPorts = 16;
-constexpr int kEpiThreads = 512;   // block size of the per-step port epilogue
+constexpr int kEpiThreads = 256;   // block size of the per-step port epilogue
+constexpr int kEpiSegPoints = 1024; // points per epilogue work item
 constexpr int kEnergyBlocks = 592; // 4 x 148 SMs: fixed partial count -> fixed sum order
 
 // Records a message for yf_last_error() and returns the status.
@@ -77,7 +79,36 @@ struct StencilParams {
 };
 
 template <typename T>
+struct FusedArgs {
+    int nx, ny, nz, px, kseg;
+    int tx0, ty0;            // first tile of this launch (tile units)
+    int z0, z1;              // planes z0..z1 of this launch
+    long plane, npts;
+    T rdx, rdy, rdz, db;
+    const uint8_t *cls[3];
+    const T *ctab;
+    const T *A;              // old buffer: 6 components at stride npts
+    T *B;                    // new buffer
+    int n, L, lo[3], hi[3];  // CPML: thickness, slab length 2n+1, faces
+    const T *prof[3];
+    T *psiE[3][2];           // E auxiliaries (in place)
+    const T *psiHr[3][2];    // H auxiliaries, read copy
+    T *psiHw[3][2];          // H auxiliaries, write copy
+};
+
+// Work item of the port epilogue: kind 0 adds the source on points [start, start+count)
+// of the source rectangle, kind 1 sums that range of a port's V surface, kind 2 of its
+// I loops; kinds 1 and 2 leave their partial sum in slot[segment].
+struct EpiSeg {
+    int kind, port, start, count;
+};
+
+template <typename T>
 struct EpiParams {
+    const EpiSeg *segs;
+    int nseg;
+    double *slots;            // one partial per segment
+    unsigned int *ticket;     // arrival counter of the blocks (reset by the last one)
     T *ez;                   // field buffer the source writes into and V reads
     const T *hy, *hz;        // H^{n+1/2}
     const uint8_t *cls_z;
@@ -108,6 +139,27 @@ template <typename T>
 cudaError_t launch_update_e(const StencilParams<T> &p, const Fields<T> &f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fused(const FusedArgs<T> &a, int tile_y, cudaStream_t s);
+// TMA-staged fused step (yf_tma.cu); tmF maps buffer A as [6][nz+1][ny+1][px] with box
+// (tma_box_x, tile_y + 2, 1, 3); tmC maps the classes [3][nz+1][ny+1][px] with box
+// (32, tile_y, 1, 3)
+template <typename T>
+int tma_box_x(int tile_x);
+cudaError_t tma_prepare();
+// second stream of a grid for work that may overlap the main stream within a step
+struct SideStream {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+template <typename T>
+cudaError_t launch_tma(const FusedArgs<T> &a, const CUtensorMap &tmF, const CUtensorMap &tmC,
+                       int tile_y, int *status, cudaStream_t s, const SideStream *side);
+// skewed TMA-staged fused step (yf_skew.cu), same tensor maps as launch_tma
+cudaError_t skew_prepare();
+template <typename T>
+cudaError_t launch_skew(const FusedArgs<T> &a, const CUtensorMap &tmF, const CUtensorMap &tmC,
+                        int tile_y, int *status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sanitize(const Fields<T> &f, uint8_t *const cls[3], int nx, int ny, int nz,
                             int px, long plane, cudaStream_t s);

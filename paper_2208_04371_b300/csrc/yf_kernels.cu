@@ -175,64 +175,86 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
 {
     __shared__ double red[kEpiThreads / 32];
     __shared__ double vi[kMaxPorts][2];
+    __shared__ bool last;
     const int tid = threadIdx.x;
     const long long n = *P.ctr;   // this is step n: E^{n+1}, H^{n+1/2} are in place
 
-    // 1. soft source E_z += A s(t_{n+1}) on plane e (Eq. 3)
-    if (P.src_kind != YF_WAVE_NONE) {
-        const double s = waveform(P.src_kind, P.p0, P.p1, P.t0, P.table, P.table_len, n + 1, P.dt);
-        const T add = (T)(P.amp * s);
-        const int nj = P.sj1 - P.sj0 + 1, nk = P.sk1 - P.sk0;
-        for (int w = tid; w < nj * nk; w += blockDim.x) {
-            const int j = P.sj0 + w % nj, k = P.sk0 + w / nj;
-            const long q = (long)k * P.plane + (long)j * P.px + P.src_plane;
-            if (P.cls_z[q]) P.ez[q] += add;
+    for (int sg = blockIdx.x; sg < P.nseg; sg += gridDim.x) {
+        const EpiSeg S = P.segs[sg];
+        if (S.kind == 0) {
+            // soft source E_z += A s(t_{n+1}) on plane e (Eq. 3)
+            const double s = waveform(P.src_kind, P.p0, P.p1, P.t0, P.table, P.table_len, n + 1, P.dt);
+            const T add = (T)(P.amp * s);
+            const int nj = P.sj1 - P.sj0 + 1;
+            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+                const int j = P.sj0 + w % nj, k = P.sk0 + w / nj;
+                const long q = (long)k * P.plane + (long)j * P.px + P.src_plane;
+                if (P.cls_z[q]) P.ez[q] += add;
+            }
+        } else if (S.kind == 1) {
+            // V: surface integral of E_z across the strip (Eq. 4), trapezoid in y
+            const PortDev d = P.ports[S.port];
+            const int nj = d.j1 - d.j0 + 1;
+            double v = 0.0;
+            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+                const int j = d.j0 + w % nj, k = d.k0 + w / nj;
+                const double wj = (j == d.j0 || j == d.j1) ? 0.5 : 1.0;
+                v += wj * (double)P.ez[(long)k * P.plane + (long)j * P.px + d.plane];
+            }
+            const double sum = block_sum(v, red);
+            if (tid == 0) P.slots[sg] = sum;
+        } else {
+            // I: loops of H at x = plane - 1/2 and plane + 1/2 (Eq. 4)
+            const PortDev d = P.ports[S.port];
+            const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
+            const int per = 2 * nyl + 2 * nzl;
+            double c = 0.0;
+            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+                const int ih = d.plane - 1 + w / per;
+                const int r = w % per;
+                if (r < 2 * nyl) {
+                    const int j = d.j0 - d.m + 1 + (r >> 1);
+                    if ((r & 1) == 0)   // bottom, along +y
+                        c += (double)P.hy[(long)(d.kb - d.m) * P.plane + (long)j * P.px + ih] * P.dy;
+                    else                // top, along -y
+                        c -= (double)P.hy[(long)(d.kt + d.m - 1) * P.plane + (long)j * P.px + ih] * P.dy;
+                } else {
+                    const int r2 = r - 2 * nyl;
+                    const int k = d.kb - d.m + 1 + (r2 >> 1);
+                    if ((r2 & 1) == 0)  // right side, along +z
+                        c += (double)P.hz[(long)k * P.plane + (long)(d.j1 + d.m - 1) * P.px + ih] * P.dz;
+                    else                // left side, along -z
+                        c -= (double)P.hz[(long)k * P.plane + (long)(d.j0 - d.m) * P.px + ih] * P.dz;
+                }
+            }
+            const double sum = block_sum(c, red);
+            if (tid == 0) P.slots[sg] = sum;
+        }
+    }
+
+    // the last block to arrive combines the partials in segment order
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid == 0) {
+        for (int p = 0; p < P.nports; ++p) { vi[p][0] = 0.0; vi[p][1] = 0.0; }
+        for (int sg = 0; sg < P.nseg; ++sg) {
+            const EpiSeg S = P.segs[sg];
+            if (S.kind == 1) vi[S.port][0] += __ldcg(P.slots + sg);
+            else if (S.kind == 2) vi[S.port][1] += __ldcg(P.slots + sg);
+        }
+        for (int p = 0; p < P.nports; ++p) {
+            const PortDev d = P.ports[p];
+            vi[p][0] = d.vscale * vi[p][0];
+            vi[p][1] = (double)d.dir * 0.5 * vi[p][1];
         }
     }
     __syncthreads();
 
-    // 2. port V (surface integral of E_z / w) and I (closed loop of H), Eq. 4
-    for (int p = 0; p < P.nports; ++p) {
-        const PortDev d = P.ports[p];
-        const int nj = d.j1 - d.j0 + 1, nk = d.k1 - d.k0;
-        double v = 0.0;
-        for (int w = tid; w < nj * nk; w += blockDim.x) {
-            const int j = d.j0 + w % nj, k = d.k0 + w / nj;
-            const double wj = (j == d.j0 || j == d.j1) ? 0.5 : 1.0;
-            v += wj * (double)P.ez[(long)k * P.plane + (long)j * P.px + d.plane];
-        }
-        const double vsum = block_sum(v, red);
-        // loops at x = plane - 1/2 (ih = plane - 1) and x = plane + 1/2 (ih = plane)
-        const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
-        const int per = 2 * nyl + 2 * nzl;
-        double c = 0.0;
-        for (int w = tid; w < 2 * per; w += blockDim.x) {
-            const int ih = d.plane - 1 + w / per;
-            const int r = w % per;
-            if (r < 2 * nyl) {
-                const int j = d.j0 - d.m + 1 + (r >> 1);
-                if ((r & 1) == 0)   // bottom, along +y
-                    c += (double)P.hy[(long)(d.kb - d.m) * P.plane + (long)j * P.px + ih] * P.dy;
-                else                // top, along -y
-                    c -= (double)P.hy[(long)(d.kt + d.m - 1) * P.plane + (long)j * P.px + ih] * P.dy;
-            } else {
-                const int r2 = r - 2 * nyl;
-                const int k = d.kb - d.m + 1 + (r2 >> 1);
-                if ((r2 & 1) == 0)  // right side, along +z
-                    c += (double)P.hz[(long)k * P.plane + (long)(d.j1 + d.m - 1) * P.px + ih] * P.dz;
-                else                // left side, along -z
-                    c -= (double)P.hz[(long)k * P.plane + (long)(d.j0 - d.m) * P.px + ih] * P.dz;
-            }
-        }
-        const double csum = block_sum(c, red);
-        if (tid == 0) {
-            vi[p][0] = d.vscale * vsum;
-            vi[p][1] = (double)d.dir * 0.5 * csum;
-        }
-        __syncthreads();
-    }
-
-    // 3. running DFT with exact integer phase: V at 2(n+1) half steps, I at 2n+1
+    // running DFT with exact integer phase: V at 2(n+1) half steps, I at 2n+1
     int total = 0;
     for (int p = 0; p < P.nports; ++p) total += P.ports[p].nfreq;
     for (int w = tid; w < total; w += blockDim.x) {
@@ -268,6 +290,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
         for (int p = 0; p < P.nports; ++p)
             if (!isfinite(vi[p][0]) || !isfinite(vi[p][1])) bad = 1;
         if (bad) atomicOr(P.status, 1);
+        *P.ticket = 0;
         *P.ctr = n + 1;
     }
 }
@@ -365,7 +388,8 @@ cudaError_t launch_update_e(const StencilParams<T> &p, const Fields<T> &f, cudaS
 template <typename T>
 cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s)
 {
-    k_epilogue<T><<<1, kEpiThreads, 0, s>>>(p);
+    const int nblk = p.nseg < 1 ? 1 : (p.nseg < 296 ? p.nseg : 296);
+    k_epilogue<T><<<nblk, kEpiThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

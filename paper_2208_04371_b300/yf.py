@@ -87,6 +87,7 @@ _SIGS = {
     "yf_read_sparams": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
+    "yf_set_variant": (_i, [_vp, _i, _i, _i]),
     "yf_profile_steps": (_i, [_vp, C.c_long, _dp, C.POINTER(_i)]),
     "yf_kernel_name": (C.c_char_p, [_vp, _i]),
     "yf_checkpoint_save": (_i, [_vp, C.c_char_p]),
@@ -307,6 +308,10 @@ def read_sparams(g, nfreq, z_ref=50.0):
                 tau=tau)
 
 
+def set_variant(g, variant, tile_y=8, kseg=16):
+    _check(_lib.yf_set_variant(C.c_void_p(g), variant, tile_y, kseg))
+
+
 def reset(g):
     _check(_lib.yf_reset(C.c_void_p(g)))
 
@@ -333,7 +338,8 @@ class Grid:
     """Owns one yf_grid handle configured from a workloads.Problem."""
 
     def __init__(self, prob, prec=FP32, stream=None, dt: Optional[float] = None,
-                 dft_mask: int = DFT_FP64, with_source: bool = True, with_ports: bool = True):
+                 dft_mask: int = DFT_FP64, with_source: bool = True, with_ports: bool = True,
+                 variant: Optional[int] = None, tile_y: int = 8, kseg: int = 16):
         self.prob = prob
         self.prec = prec
         if dt is None:
@@ -358,6 +364,8 @@ class Grid:
                              p.margin, prob.freqs, p.width)
                     self.nports += 1
             set_dft_mode(self.h, dft_mask)
+            if variant is not None:
+                set_variant(self.h, variant, tile_y, kseg)
         except Exception:
             grid_destroy(self.h)
             self.h = None

@@ -129,10 +129,21 @@ def _ragged_problem():
     return p
 
 
-def test_ragged_lossy_grid_fp64_parity(gpu):
+@pytest.fixture(scope="module")
+def ragged_ref():
     p = _ragged_problem()
-    ref = yee.run(p, want_fields=True)
-    with gpu.Grid(p, prec=gpu.FP64) as g:
+    return p, yee.run(p, want_fields=True)
+
+
+@pytest.mark.parametrize("variant,tile_y,kseg", [(0, 8, 64), (1, 8, 64), (1, 4, 5), (1, 16, 7),
+                                                 (2, 8, 64), (2, 4, 5), (2, 16, 7), (2, 8, 1),
+                                                 (3, 8, 64), (3, 4, 5), (3, 16, 7), (3, 8, 1),
+                                                 (3, 4, 2)])
+def test_ragged_lossy_grid_fp64_parity(gpu, ragged_ref, variant, tile_y, kseg):
+    """Reference and fused kernels, several tiles and z-segment lengths (segment starts
+    recompute the plane below), against the oracle on a ragged lossy grid."""
+    p, ref = ragged_ref
+    with gpu.Grid(p, prec=gpu.FP64, variant=variant, tile_y=tile_y, kseg=kseg) as g:
         g.step(p.nsteps)
         g.sync()
         f = g.fields()
@@ -180,6 +191,20 @@ def test_dft_accumulator_variants_agree(gpu):
     scale = np.max(np.abs(V64))
     assert np.max(np.abs(Vk - V64)) < 1e-6 * scale
     assert np.max(np.abs(V32 - V64)) < 1e-4 * scale
+
+
+@pytest.mark.parametrize("variant,tile_y", [(0, 8), (1, 8), (2, 4), (2, 8), (2, 16), (3, 4),
+                                            (3, 8), (3, 16)])
+def test_fp32_variants_match_oracle_while_pulse_is_inside(gpu, ragged_ref, variant, tile_y):
+    """Every FP32 kernel variant against the FP64 oracle at step 40 (the Eq. 3 pulse peaks at
+    step 13 here, so the fields are still large): relative L2 <= 1e-5."""
+    p, _ = ragged_ref
+    ref = yee.run(p, nsteps=40, want_fields=True)["fields"]
+    with gpu.Grid(p, prec=gpu.FP32, variant=variant, tile_y=tile_y, kseg=9) as g:
+        g.step(40)
+        g.sync()
+        f = g.fields()
+    assert rel_l2(f, ref) <= 1e-5
 
 
 def test_graph_chunks_equal_single_steps(gpu):
