@@ -160,9 +160,17 @@ yf_status yf_set_dft_mode(yf_grid *g, int mask);
  *      computation; a bounded wait that expires makes yf_sync return YF_E_TIMEOUT;
  *   3  as 2, skewed by one plane (H on plane t and E on plane t-1 per iteration, one block
  *      barrier per plane, CPML auxiliaries fetched ahead of the arithmetic).
- * tile_y in {4, 8, 16}, kseg >= 1.  All variants compute the same update; results agree to
+ * tile_y in {4, 8, 16}, 1 <= kseg <= 64.  All variants compute the same update; results agree to
  * rounding.  Drops captured graphs; may be called between steps. */
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg);
+
+/* Autotuner (before the first step): times the TMA-staged fused step (variant 2) for
+ * tile_y in {4, 8, 16} x kseg in {8, 16, 32} over `reps` steps each with CUDA events, keeps
+ * the fastest, resets fields, auxiliaries, spectra and the step count to zero, and caches the
+ * choice in the JSON file cache_path (NULL: no cache) under a key of precision, size bucket
+ * (cells rounded up to a power of two) and presence of absorbing slabs; a cached key skips
+ * the timing.  The chosen tile_y and kseg are returned (either pointer may be NULL). */
+yf_status yf_autotune(yf_grid *g, const char *cache_path, int reps, int *tile_y, int *kseg);
 
 /* Advance n time steps asynchronously on the handle's stream (Sec. II-A time loop:
  * H half step, E half step, source, port sampling, DFT accumulation).  Steps are
@@ -248,6 +256,53 @@ const char *yf_kernel_name(yf_grid *g, int idx);
  * load requires a grid created and configured identically. */
 yf_status yf_checkpoint_save(yf_grid *g, const char *path);
 yf_status yf_checkpoint_load(yf_grid *g, const char *path);
+
+/* ---- batched solve of many independent lines (one shared time step) --------------------
+ * Each instance is configured exactly as a single grid would be (the fields below map to
+ * yf_set_materials, yf_add_pec_sheet, yf_set_boundaries, yf_set_pml, yf_set_source and
+ * yf_add_port); all instances advance together: per step one launch over the CPML-free
+ * interior work of every instance, one over the CPML frames, one port epilogue with a block
+ * per instance; chunks of steps replay from captured CUDA graphs. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    const uint8_t *ids;           /* host, nz*ny*nx; NULL keeps vacuum */
+    int nmat;
+    const double *eps_r, *sigma, *mu_r;   /* mu_r may be NULL */
+    const uint8_t *is_pec;        /* may be NULL */
+    int nsheets;
+    const int *sheets;            /* nsheets x {normal_axis, index, lo0, hi0, lo1, hi1} */
+    int bc[6];
+    int pml_cells, pml_order;
+    double pml_sigma_scale, pml_kappa_max, pml_alpha_max;
+    int src_plane, src_j0, src_j1, src_k0, src_k1;
+    yf_waveform src;              /* kind YF_WAVE_NONE: no source */
+    int nports;
+    const yf_port_desc *ports;
+    int nfreq;                    /* one frequency list shared by the instance's ports */
+    const double *freqs;
+} yf_instance_desc;
+
+typedef struct yf_batch yf_batch;
+
+/* dt <= 0 selects 0.99 of the smallest Courant limit among the instances; a dt above any
+ * instance's limit returns YF_E_UNSTABLE.  Fields of every instance start at zero. */
+yf_status yf_batch_create(int n, const yf_instance_desc *d, double dt, yf_prec prec, void *stream,
+                          yf_batch **out);
+yf_status yf_batch_destroy(yf_batch *b);
+/* Tile height (4, 8, 16) and z-planes per work item; defaults 8 and 16. */
+yf_status yf_batch_set_tiling(yf_batch *b, int tile_y, int kseg);
+yf_status yf_batch_step(yf_batch *b, long n);
+/* YF_E_TIMEOUT / YF_E_UNSTABLE as for single grids (any instance). */
+yf_status yf_batch_sync(yf_batch *b);
+yf_status yf_batch_info(yf_batch *b, int *n, long *cells, double *dt, long *steps);
+/* The instance's grid handle (owned by the batch) for the single-grid read-out calls
+ * (yf_read_fields, yf_read_port_dft, yf_read_sparams, yf_energy). */
+yf_status yf_batch_grid(yf_batch *b, int inst, yf_grid **g);
+yf_status yf_batch_read_port_dft(yf_batch *b, int inst, int port, int kind, double *V_re,
+                                 double *V_im, double *I_re, double *I_im);
+/* As yf_autotune, for the batch (key over the batch's total cells). */
+yf_status yf_batch_autotune(yf_batch *b, const char *cache_path, int reps, int *tile_y, int *kseg);
 
 #ifdef __cplusplus
 }

@@ -150,7 +150,7 @@ static yf_status build_pml(yf_grid *g)
 }
 
 // tensor maps of the TMA-staged step, for the grid's current tile height
-static yf_status encode_maps(yf_grid *g)
+yf_status encode_maps(yf_grid *g)
 {
     if (g->tmap_tile_y == g->tile_y) return YF_OK;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -186,17 +186,25 @@ static yf_status encode_maps(yf_grid *g)
     if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding the class tensor map failed (%d)", (int)r);
     YF_CUDA_TRY(tma_prepare());
     YF_CUDA_TRY(skew_prepare());
-    if (!g->side.stream) {
-        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
-    }
     g->tmap_tile_y = g->tile_y;
     return YF_OK;
 }
 
+static yf_status ensure_plan(yf_grid *g)
+{
+    if (g->plan_ok) return YF_OK;
+    yf_status st = encode_maps(g);
+    if (st != YF_OK) return st;
+    std::vector<yf_grid *> one(1, g);
+    st = g->prec == YF_FP32 ? build_plan<float>(one, g->tile_y, g->kseg, &g->plan)
+                            : build_plan<double>(one, g->tile_y, g->kseg, &g->plan);
+    if (st != YF_OK) return st;
+    g->plan_ok = true;
+    return YF_OK;
+}
+
 template <typename T>
-static Fields<T> fields_of(const yf_grid *g, int b)
+Fields<T> fields_of(const yf_grid *g, int b)
 {
     Fields<T> F;
     for (int c = 0; c < 6; ++c) F.c[c] = (T *)((char *)g->buf[b] + (size_t)c * g->npts * g->esz);
@@ -204,7 +212,7 @@ static Fields<T> fields_of(const yf_grid *g, int b)
 }
 
 template <typename T>
-static StencilParams<T> stencil_params(const yf_grid *g)
+StencilParams<T> stencil_params(const yf_grid *g)
 {
     StencilParams<T> P;
     P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.px = g->px; P.plane = g->plane;
@@ -227,7 +235,7 @@ static StencilParams<T> stencil_params(const yf_grid *g)
 }
 
 template <typename T>
-static FusedArgs<T> fused_args(const yf_grid *g)
+FusedArgs<T> fused_args(const yf_grid *g)
 {
     FusedArgs<T> F;
     F.nx = g->nx; F.ny = g->ny; F.nz = g->nz; F.px = g->px; F.kseg = g->kseg;
@@ -255,7 +263,7 @@ static FusedArgs<T> fused_args(const yf_grid *g)
 }
 
 template <typename T>
-static EpiParams<T> epi_params(const yf_grid *g)
+EpiParams<T> epi_params(const yf_grid *g)
 {
     EpiParams<T> E;
     E.segs = g->segs_dev; E.nseg = (int)g->segs.size(); E.slots = g->slots; E.ticket = g->ticket;
@@ -273,6 +281,13 @@ static EpiParams<T> epi_params(const yf_grid *g)
     E.ctr = g->ctr; E.status = g->status;
     return E;
 }
+
+template Fields<float> fields_of<float>(const yf_grid *, int);
+template Fields<double> fields_of<double>(const yf_grid *, int);
+template FusedArgs<float> fused_args<float>(const yf_grid *);
+template FusedArgs<double> fused_args<double>(const yf_grid *);
+template EpiParams<float> epi_params<float>(const yf_grid *);
+template EpiParams<double> epi_params<double>(const yf_grid *);
 
 // epilogue work items: source rectangle, each port's V surface and I loops
 static void build_segments(yf_grid *g)
@@ -349,6 +364,16 @@ yf_status finalize(yf_grid *g)
         if (st != YF_OK) return st;
     }
     g->started = true;
+    if (g->variant == 2) {
+        st = ensure_plan(g);
+        if (st != YF_OK) return st;
+    }
+    if (g->variant == 2 && !g->side.stream) {
+        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
+    }
+    g->started = true;
     return YF_OK;
 }
 
@@ -360,7 +385,7 @@ static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
         if (g->variant == 3)
             e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, s);
         else if (g->variant == 2)
-            e = launch_tma<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, s, &g->side);
+            e = launch_tma_plan<T>(g->plan, g->tile_y, g->cur, g->status, s, &g->side);
         else
             e = launch_fused<T>(fused_args<T>(g), g->tile_y, s);
         if (e != cudaSuccess) return e;
@@ -377,7 +402,30 @@ static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
     return launch_epilogue<T>(epi_params<T>(g), s);
 }
 
-static cudaError_t step_direct(yf_grid *g, cudaStream_t s)
+// zero fields, CPML auxiliaries, accumulators, counters (geometry and set-up kept)
+yf_status reset_state(yf_grid *g)
+{
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int b = 0; b < 2; ++b) YF_CUDA_TRY(cudaMemsetAsync(g->buf[b], 0, 6 * g->npts * g->esz, g->stream));
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 2; ++q) {
+            void *ps[3] = {g->psiE[a][q], g->psiH[0][a][q], g->psiH[1][a][q]};
+            for (void *p : ps)
+                if (p) YF_CUDA_TRY(cudaMemsetAsync(p, 0, g->psi_count[a] * g->esz, g->stream));
+        }
+    if (g->nf_total > 0) {
+        YF_CUDA_TRY(cudaMemsetAsync(g->acc64, 0, (size_t)g->nf_total * 4 * sizeof(double), g->stream));
+        YF_CUDA_TRY(cudaMemsetAsync(g->acc32, 0, (size_t)g->nf_total * 4 * sizeof(float), g->stream));
+        YF_CUDA_TRY(cudaMemsetAsync(g->kahan, 0, (size_t)g->nf_total * 8 * sizeof(float), g->stream));
+    }
+    YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(long long), g->stream));
+    YF_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), g->stream));
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->steps_done = 0;
+    return YF_OK;
+}
+
+cudaError_t step_direct(yf_grid *g, cudaStream_t s)
 {
     return g->prec == YF_FP32 ? launch_one_step<float>(g, s) : launch_one_step<double>(g, s);
 }
@@ -480,6 +528,7 @@ yf_status yf_grid_destroy(yf_grid *g)
         }
     }
     cudaFree(g->segs_dev); cudaFree(g->slots); cudaFree(g->ticket);
+    free_plan(&g->plan);
     if (g->side.stream) {
         cudaStreamSynchronize(g->side.stream);
         cudaEventDestroy(g->side.fork);
@@ -814,23 +863,8 @@ yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, d
 yf_status yf_reset(yf_grid *g)
 {
     if (!g) return fail(YF_E_INVALID, "yf_reset: NULL grid");
-    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (int b = 0; b < 2; ++b) YF_CUDA_TRY(cudaMemsetAsync(g->buf[b], 0, 6 * g->npts * g->esz, g->stream));
-    for (int a = 0; a < 3; ++a)
-        for (int q = 0; q < 2; ++q) {
-            void *ps[3] = {g->psiE[a][q], g->psiH[0][a][q], g->psiH[1][a][q]};
-            for (void *p : ps)
-                if (p) YF_CUDA_TRY(cudaMemsetAsync(p, 0, g->psi_count[a] * g->esz, g->stream));
-        }
-    if (g->nf_total > 0) {
-        YF_CUDA_TRY(cudaMemsetAsync(g->acc64, 0, (size_t)g->nf_total * 4 * sizeof(double), g->stream));
-        YF_CUDA_TRY(cudaMemsetAsync(g->acc32, 0, (size_t)g->nf_total * 4 * sizeof(float), g->stream));
-        YF_CUDA_TRY(cudaMemsetAsync(g->kahan, 0, (size_t)g->nf_total * 8 * sizeof(float), g->stream));
-    }
-    YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(long long), g->stream));
-    YF_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), g->stream));
-    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    g->steps_done = 0;
+    yf_status st = reset_state(g);
+    if (st != YF_OK) return st;
     g->sheets.clear();
     g->geometry_open = true;
     return YF_OK;
@@ -847,7 +881,7 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
         if (g->variant == 3)
             e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream);
         else if (g->variant == 2)
-            e = launch_tma<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream, &g->side);
+            e = launch_tma_plan<T>(g->plan, g->tile_y, g->cur, g->status, g->stream, &g->side);
         else
             e = launch_fused<T>(fused_args<T>(g), g->tile_y, g->stream);
         if (e != cudaSuccess) return e;
@@ -916,14 +950,30 @@ yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
     if (!g) return fail(YF_E_INVALID, "yf_set_variant: NULL grid");
     if (variant < 0 || variant > 3) return fail(YF_E_INVALID, "yf_set_variant: variant must be 0..3");
     if (tile_y != 4 && tile_y != 8 && tile_y != 16) return fail(YF_E_INVALID, "yf_set_variant: tile_y must be 4, 8 or 16");
-    if (kseg < 1) return fail(YF_E_INVALID, "yf_set_variant: kseg must be >= 1");
+    if (kseg < 1 || kseg > kMaxKseg) return fail(YF_E_INVALID, "yf_set_variant: kseg must be 1..%d", kMaxKseg);
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     for (int b = 0; b < 2; ++b)
         if (g->graph[b]) { cudaGraphExecDestroy(g->graph[b]); g->graph[b] = nullptr; }
     g->variant = variant;
     g->tile_y = tile_y;
     g->kseg = kseg;
-    if (g->started && variant >= 2) return encode_maps(g);
+    if (g->plan_ok) {
+        free_plan(&g->plan);
+        g->plan_ok = false;
+    }
+    if (g->started && variant >= 2) {
+        yf_status st = encode_maps(g);
+        if (st != YF_OK) return st;
+    }
+    if (g->started && variant == 2) {
+        yf_status st = ensure_plan(g);
+        if (st != YF_OK) return st;
+    }
+    if (g->started && variant == 2 && !g->side.stream) {
+        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
+        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
+    }
     return YF_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "yf_internal.h"
@@ -76,7 +77,9 @@ struct yf_grid {
     CUtensorMap tmF[2];           // field buffers as 4-D tensors (variant 2)
     CUtensorMap tmC;              // edge classes as a 4-D tensor
     int tmap_tile_y = 0;          // tile the maps were encoded for (0: not encoded)
-    yf::SideStream side = {};     // frame launches of variant 2 overlap the interior
+    yf::SideStream side = {};     // CPML work of variant 2 overlaps the interior
+    yf::TmaPlan plan = {};        // work items / arguments / maps of variant 2 (a batch of one)
+    bool plan_ok = false;
     int tile_y = 8;               // fused: block rows (block is 32 x tile_y)
     int kseg = 16;                // fused: z-planes per block
     int chunk = 32;               // steps per captured graph (even)
@@ -85,6 +88,24 @@ struct yf_grid {
 
 namespace yf {
 yf_status finalize(yf_grid *g);
+yf_status encode_maps(yf_grid *g);
+yf_status reset_state(yf_grid *g);
+cudaError_t step_direct(yf_grid *g, cudaStream_t s);   // one un-graphed step
+// autotuner cache (yf_tune.cu): "key": [tile_y, kseg, ms] entries in a small JSON object
+bool tune_cache_get(const char *path, const std::string &key, int *tile_y, int *kseg);
+void tune_cache_put(const char *path, const std::string &key, int tile_y, int kseg, double ms);
+std::string tune_key(const char *kind, yf_prec prec, long cells, int pml);
+// plan of the TMA-staged step over the given grids (yf_batch.cu); tensor maps must be encoded
+// for tile_y
+template <typename T>
+yf_status build_plan(const std::vector<yf_grid *> &grids, int tile_y, int kseg, TmaPlan *pl);
+void free_plan(TmaPlan *pl);
+template <typename T>
+Fields<T> fields_of(const yf_grid *g, int b);
+template <typename T>
+FusedArgs<T> fused_args(const yf_grid *g);   // A = buf[cur], psi H read = psiH[hpar]
+template <typename T>
+EpiParams<T> epi_params(const yf_grid *g);   // fields of buf[cur]
 double courant_limit_dt(double dx, double dy, double dz);
 // uniform-line two-port extraction from FP64 DFTs laid out as
 // [port][Vre, Vim, Ire, Iim][nf] (yf_sparams.cu)

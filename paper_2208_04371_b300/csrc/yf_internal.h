@@ -19,6 +19,7 @@ constexpr double kEps0 = 8.8541878128e-12;
 
 constexpr int kMaxClasses = 256;   // uint8 edge classes, class 0 = PEC
 constexpr int kMaxPorts = 16;
+constexpr int kMaxKseg = 64;      // z-planes per block of the fused steps
 constexpr int kEpiThreads = 256;   // block size of the per-step port epilogue
 constexpr int kEpiSegPoints = 1024; // points per epilogue work item
 constexpr int kEnergyBlocks = 592; // 4 x 148 SMs: fixed partial count -> fixed sum order
@@ -139,6 +140,9 @@ template <typename T>
 cudaError_t launch_update_e(const StencilParams<T> &p, const Fields<T> &f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s);
+// one block per grid; eps holds two parameter sets (buffer parity 0, 1) per grid
+template <typename T>
+cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fused(const FusedArgs<T> &a, int tile_y, cudaStream_t s);
 // TMA-staged fused step (yf_tma.cu); tmF maps buffer A as [6][nz+1][ny+1][px] with box
@@ -152,9 +156,24 @@ struct SideStream {
     cudaStream_t stream;
     cudaEvent_t fork, join;
 };
+// one block of the TMA-staged step: instance, tile origin (node indices), planes kb..ke
+struct BatchItem {
+    int inst, i0, j0, kb, ke;
+};
+// device-side plan of the TMA-staged step for one or many grids: work items grouped by kind
+// (0 no CPML, 1 x CPML, 2 y CPML, 3 z CPML, 4 all), per-grid arguments for both buffer
+// parities and per-grid tensor maps [grid][parity][field map, class map]
+struct TmaPlan {
+    BatchItem *items;
+    int offset[5], count[5];
+    void *args;
+    CUtensorMap *maps;
+};
 template <typename T>
-cudaError_t launch_tma(const FusedArgs<T> &a, const CUtensorMap &tmF, const CUtensorMap &tmC,
-                       int tile_y, int *status, cudaStream_t s, const SideStream *side);
+cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *status, cudaStream_t s,
+                            const SideStream *side);
+void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
+               const int hi[3], std::vector<BatchItem> items[5]);
 // skewed TMA-staged fused step (yf_skew.cu), same tensor maps as launch_tma
 cudaError_t skew_prepare();
 template <typename T>

@@ -170,91 +170,66 @@ __device__ __forceinline__ void kahan_add(float *sum, float *comp, float x)
     *sum = t;
 }
 
+// One work item of the epilogue: kind 0 adds the source on its points; kinds 1 and 2 return
+// the block's partial V or I sum (valid in thread 0).
 template <typename T>
-__global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
+__device__ double epi_segment(const EpiParams<T> &P, const EpiSeg &S, long long n, double *red)
 {
-    __shared__ double red[kEpiThreads / 32];
-    __shared__ double vi[kMaxPorts][2];
-    __shared__ bool last;
     const int tid = threadIdx.x;
-    const long long n = *P.ctr;   // this is step n: E^{n+1}, H^{n+1/2} are in place
-
-    for (int sg = blockIdx.x; sg < P.nseg; sg += gridDim.x) {
-        const EpiSeg S = P.segs[sg];
-        if (S.kind == 0) {
-            // soft source E_z += A s(t_{n+1}) on plane e (Eq. 3)
-            const double s = waveform(P.src_kind, P.p0, P.p1, P.t0, P.table, P.table_len, n + 1, P.dt);
-            const T add = (T)(P.amp * s);
-            const int nj = P.sj1 - P.sj0 + 1;
-            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
-                const int j = P.sj0 + w % nj, k = P.sk0 + w / nj;
-                const long q = (long)k * P.plane + (long)j * P.px + P.src_plane;
-                if (P.cls_z[q]) P.ez[q] += add;
+    if (S.kind == 0) {
+        // soft source E_z += A s(t_{n+1}) on plane e (Eq. 3)
+        const double s = waveform(P.src_kind, P.p0, P.p1, P.t0, P.table, P.table_len, n + 1, P.dt);
+        const T add = (T)(P.amp * s);
+        const int nj = P.sj1 - P.sj0 + 1;
+        for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+            const int j = P.sj0 + w % nj, k = P.sk0 + w / nj;
+            const long q = (long)k * P.plane + (long)j * P.px + P.src_plane;
+            if (P.cls_z[q]) P.ez[q] += add;
+        }
+        return 0.0;
+    }
+    const PortDev d = P.ports[S.port];
+    double acc = 0.0;
+    if (S.kind == 1) {
+        // V: surface integral of E_z across the strip (Eq. 4), trapezoid in y
+        const int nj = d.j1 - d.j0 + 1;
+        for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+            const int j = d.j0 + w % nj, k = d.k0 + w / nj;
+            const double wj = (j == d.j0 || j == d.j1) ? 0.5 : 1.0;
+            acc += wj * (double)P.ez[(long)k * P.plane + (long)j * P.px + d.plane];
+        }
+    } else {
+        // I: loops of H at x = plane - 1/2 and plane + 1/2 (Eq. 4)
+        const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
+        const int per = 2 * nyl + 2 * nzl;
+        for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
+            const int ih = d.plane - 1 + w / per;
+            const int r = w % per;
+            if (r < 2 * nyl) {
+                const int j = d.j0 - d.m + 1 + (r >> 1);
+                if ((r & 1) == 0)   // bottom, along +y
+                    acc += (double)P.hy[(long)(d.kb - d.m) * P.plane + (long)j * P.px + ih] * P.dy;
+                else                // top, along -y
+                    acc -= (double)P.hy[(long)(d.kt + d.m - 1) * P.plane + (long)j * P.px + ih] * P.dy;
+            } else {
+                const int r2 = r - 2 * nyl;
+                const int k = d.kb - d.m + 1 + (r2 >> 1);
+                if ((r2 & 1) == 0)  // right side, along +z
+                    acc += (double)P.hz[(long)k * P.plane + (long)(d.j1 + d.m - 1) * P.px + ih] * P.dz;
+                else                // left side, along -z
+                    acc -= (double)P.hz[(long)k * P.plane + (long)(d.j0 - d.m) * P.px + ih] * P.dz;
             }
-        } else if (S.kind == 1) {
-            // V: surface integral of E_z across the strip (Eq. 4), trapezoid in y
-            const PortDev d = P.ports[S.port];
-            const int nj = d.j1 - d.j0 + 1;
-            double v = 0.0;
-            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
-                const int j = d.j0 + w % nj, k = d.k0 + w / nj;
-                const double wj = (j == d.j0 || j == d.j1) ? 0.5 : 1.0;
-                v += wj * (double)P.ez[(long)k * P.plane + (long)j * P.px + d.plane];
-            }
-            const double sum = block_sum(v, red);
-            if (tid == 0) P.slots[sg] = sum;
-        } else {
-            // I: loops of H at x = plane - 1/2 and plane + 1/2 (Eq. 4)
-            const PortDev d = P.ports[S.port];
-            const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
-            const int per = 2 * nyl + 2 * nzl;
-            double c = 0.0;
-            for (int w = S.start + tid; w < S.start + S.count; w += blockDim.x) {
-                const int ih = d.plane - 1 + w / per;
-                const int r = w % per;
-                if (r < 2 * nyl) {
-                    const int j = d.j0 - d.m + 1 + (r >> 1);
-                    if ((r & 1) == 0)   // bottom, along +y
-                        c += (double)P.hy[(long)(d.kb - d.m) * P.plane + (long)j * P.px + ih] * P.dy;
-                    else                // top, along -y
-                        c -= (double)P.hy[(long)(d.kt + d.m - 1) * P.plane + (long)j * P.px + ih] * P.dy;
-                } else {
-                    const int r2 = r - 2 * nyl;
-                    const int k = d.kb - d.m + 1 + (r2 >> 1);
-                    if ((r2 & 1) == 0)  // right side, along +z
-                        c += (double)P.hz[(long)k * P.plane + (long)(d.j1 + d.m - 1) * P.px + ih] * P.dz;
-                    else                // left side, along -z
-                        c -= (double)P.hz[(long)k * P.plane + (long)(d.j0 - d.m) * P.px + ih] * P.dz;
-                }
-            }
-            const double sum = block_sum(c, red);
-            if (tid == 0) P.slots[sg] = sum;
         }
     }
+    return block_sum(acc, red);
+}
 
-    // the last block to arrive combines the partials in segment order
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (tid == 0) {
-        for (int p = 0; p < P.nports; ++p) { vi[p][0] = 0.0; vi[p][1] = 0.0; }
-        for (int sg = 0; sg < P.nseg; ++sg) {
-            const EpiSeg S = P.segs[sg];
-            if (S.kind == 1) vi[S.port][0] += __ldcg(P.slots + sg);
-            else if (S.kind == 2) vi[S.port][1] += __ldcg(P.slots + sg);
-        }
-        for (int p = 0; p < P.nports; ++p) {
-            const PortDev d = P.ports[p];
-            vi[p][0] = d.vscale * vi[p][0];
-            vi[p][1] = (double)d.dir * 0.5 * vi[p][1];
-        }
-    }
-    __syncthreads();
-
-    // running DFT with exact integer phase: V at 2(n+1) half steps, I at 2n+1
+// Running DFT with exact integer phase (V at 2(n+1) half steps, I at 2n+1), then the
+// finite check and the step counter; vi holds each port's V and I.
+template <typename T>
+__device__ void epi_finish(const EpiParams<T> &P, long long n, const double (*vi)[2])
+{
+    const int tid = threadIdx.x;
     int total = 0;
     for (int p = 0; p < P.nports; ++p) total += P.ports[p].nfreq;
     for (int w = tid; w < total; w += blockDim.x) {
@@ -290,9 +265,76 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
         for (int p = 0; p < P.nports; ++p)
             if (!isfinite(vi[p][0]) || !isfinite(vi[p][1])) bad = 1;
         if (bad) atomicOr(P.status, 1);
-        *P.ticket = 0;
         *P.ctr = n + 1;
     }
+}
+
+template <typename T>
+__device__ void epi_scale(const EpiParams<T> &P, double (*vi)[2])
+{
+    for (int p = 0; p < P.nports; ++p) {
+        const PortDev d = P.ports[p];
+        vi[p][0] = d.vscale * vi[p][0];
+        vi[p][1] = (double)d.dir * 0.5 * vi[p][1];
+    }
+}
+
+// Single grid: the segments are spread over the blocks; each V/I partial lands in its own
+// slot and the last block to arrive combines them in segment order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
+{
+    __shared__ double red[kEpiThreads / 32];
+    __shared__ double vi[kMaxPorts][2];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const long long n = *P.ctr;   // this is step n: E^{n+1}, H^{n+1/2} are in place
+    for (int sg = blockIdx.x; sg < P.nseg; sg += gridDim.x) {
+        const double part = epi_segment(P, P.segs[sg], n, red);
+        if (tid == 0 && P.segs[sg].kind != 0) P.slots[sg] = part;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid == 0) {
+        for (int p = 0; p < P.nports; ++p) { vi[p][0] = 0.0; vi[p][1] = 0.0; }
+        for (int sg = 0; sg < P.nseg; ++sg) {
+            const EpiSeg S = P.segs[sg];
+            if (S.kind == 1) vi[S.port][0] += __ldcg(P.slots + sg);
+            else if (S.kind == 2) vi[S.port][1] += __ldcg(P.slots + sg);
+        }
+        epi_scale(P, vi);
+        *P.ticket = 0;
+    }
+    __syncthreads();
+    epi_finish(P, n, vi);
+}
+
+// Many grids: block b runs the whole epilogue of grid b (parameters of the current parity).
+template <typename T>
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue_batch(const EpiParams<T> *eps, int parity)
+{
+    __shared__ double red[kEpiThreads / 32];
+    __shared__ double vi[kMaxPorts][2];
+    const EpiParams<T> P = eps[2 * blockIdx.x + parity];
+    const int tid = threadIdx.x;
+    const long long n = *P.ctr;
+    if (tid == 0)
+        for (int p = 0; p < P.nports; ++p) { vi[p][0] = 0.0; vi[p][1] = 0.0; }
+    for (int sg = 0; sg < P.nseg; ++sg) {
+        const EpiSeg S = P.segs[sg];
+        const double part = epi_segment(P, S, n, red);
+        if (tid == 0) {
+            if (S.kind == 1) vi[S.port][0] += part;
+            else if (S.kind == 2) vi[S.port][1] += part;
+        }
+    }
+    if (tid == 0) epi_scale(P, vi);
+    __syncthreads();
+    epi_finish(P, n, vi);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -362,6 +404,14 @@ __global__ void k_sanitize(Fields<T> F, const uint8_t *cx, const uint8_t *cy, co
 }  // namespace
 
 template <typename T>
+cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_epilogue_batch<T><<<n, kEpiThreads, 0, s>>>(eps, parity);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_sanitize(const Fields<T> &f, uint8_t *const cls[3], int nx, int ny, int nz,
                             int px, long plane, cudaStream_t s)
 {
@@ -415,6 +465,7 @@ cudaError_t launch_energy(const T *const c[6], const uint8_t *const cls[3], cons
     template cudaError_t launch_update_e<T>(const StencilParams<T> &, const Fields<T> &,     \
                                             cudaStream_t);                                  \
     template cudaError_t launch_epilogue<T>(const EpiParams<T> &, cudaStream_t);            \
+    template cudaError_t launch_epilogue_batch<T>(const EpiParams<T> *, int, int, cudaStream_t); \
     template cudaError_t launch_sanitize<T>(const Fields<T> &, uint8_t *const[3], int, int, \
                                             int, int, long, cudaStream_t);                  \
     template cudaError_t launch_energy<T>(const T *const[6], const uint8_t *const[3],        \

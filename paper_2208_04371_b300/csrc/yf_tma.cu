@@ -15,6 +15,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "yf_internal.h"
 
 namespace yf {
@@ -101,7 +104,11 @@ struct TmaLayout {
     static constexpr int SH_OFF = NST * STAGE;            // new H window
     static constexpr int CT_OFF = SH_OFF + WIN_PAD;       // (Ca, Cb) pairs
     static constexpr int BAR_OFF = CT_OFF + (2 * kMaxClasses * (int)sizeof(T) + 127) / 128 * 128;
-    static constexpr int BYTES = BAR_OFF + 64;
+    // CPML profiles of the block: x [6][BX], y [6][WY], z [6][ZMAX] (planes kb-1 .. ke)
+    static constexpr int ZMAX = kMaxKseg + 2;
+    static constexpr int PR_OFF = BAR_OFF + 64;
+    static constexpr int PR_BYTES = (6 * (BX + WY + ZMAX) * (int)sizeof(T) + 15) / 16 * 16;
+    static constexpr int BYTES = PR_OFF + PR_BYTES;
     static constexpr uint32_t TX_BYTES = 2 * WIN_BYTES + CLS_BYTES;
 };
 
@@ -109,40 +116,47 @@ template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
 template <> struct Pair<double> { using type = double2; };
 
-// CPML-corrected derivative of an H component without the auxiliary write (halo nodes and
-// the warm-up plane recompute values whose owner writes the auxiliaries).
+// CPML term from a staged profile: pr holds b, a, 1/kappa at integer nodes (rows 0..2) and at
+// half nodes (rows 3..5), `stride` entries per row.  psi_new = b psi + a d (stored at w when
+// given); returns d / kappa + psi_new.
 template <typename T>
-__device__ __forceinline__ T read_term(T d, const T *psi, long o, const T *prof, int N1, int p)
+__device__ __forceinline__ T cpt(T d, T psi, T *w, const T *pr, int stride, int which, int idx)
 {
-    return cpml_x<T>(d, psi + o, (T *)nullptr, prof, N1, 3, p);
+    const T v = pr[which * stride + idx] * psi + pr[(which + 1) * stride + idx] * d;
+    if (w) *w = v;
+    return d * pr[(which + 2) * stride + idx] + v;
 }
 
 // Block: TX x TYT threads; thread (tx, ty) owns node column i = i0 + tx and the CY rows
 // j = j0 + ty*CY + r (r < CY) of a TX x (TYT*CY) tile.  Rows of one thread are contiguous, so
 // the y neighbours of its E and H values come from registers, E^n read for the H update is
 // reused by the E update, and the loop overhead of a plane is paid once per CY nodes.
-template <typename T, int TX, int TYT, int CY, bool HP>
-__global__ void __launch_bounds__(TX *TYT)
-    k_yee_tma(FusedArgs<T> P, const __grid_constant__ CUtensorMap tmF,
-              const __grid_constant__ CUtensorMap tmC, int *status)
+// HP (absorbing slabs present): the block's CPML profiles sit in shared memory and each
+// thread fetches the auxiliaries of plane p+1 while it computes plane p.
+template <typename T, int TX, int TYT, int CY, int PM>
+__device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMap *tmF,
+                                         const CUtensorMap *tmC, int *status, unsigned char *sm,
+                                         int i0, int j0, int kb, int ke)
 {
     constexpr int TY = TYT * CY;
+    // PM: CPML code compiled in for the x (1), y (2) and z (4) slabs
+    constexpr bool HPX = (PM & 1) != 0, HPY = (PM & 2) != 0, HPZ = (PM & 4) != 0;
+    constexpr bool HP = PM != 0;
     using Lay = TmaLayout<T, TX, TY>;
     using P2 = typename Pair<T>::type;
-    constexpr int XO = Lay::XO, BX = Lay::BX, WN = Lay::WN, NT = TX * TYT;
-    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int XO = Lay::XO, BX = Lay::BX, WN = Lay::WN, WY = Lay::WY, NT = TX * TYT;
+    constexpr int ZMAX = Lay::ZMAX;
     T *sHn = reinterpret_cast<T *>(sm + Lay::SH_OFF);
     P2 *sC = reinterpret_cast<P2 *>(sm + Lay::CT_OFF);
+    T *PX = reinterpret_cast<T *>(sm + Lay::PR_OFF);   // [6][BX]
+    T *PY = PX + 6 * BX;                                  // [6][WY]
+    T *PZ = PY + 6 * WY;                                  // [6][ZMAX]
     const uint32_t bar0 = smem_u32(sm + Lay::BAR_OFF);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = (blockIdx.x + P.tx0) * TX, j0 = (blockIdx.y + P.ty0) * TY;
     const int i = i0 + tx, jb = j0 + ty * CY;
-    const int kb = P.z0 + blockIdx.z * P.kseg;
-    if (kb > P.z1) return;
-    const int ke = min(P.z1, kb + P.kseg - 1);
     const long plane = P.plane, npts = P.npts;
-    const int px = P.px, NX1 = P.nx + 1, NY1 = P.ny + 1, NZ1 = P.nz + 1;
+    const int px = P.px, NX1 = P.nx + 1, NY1 = P.ny + 1;
     const int n = P.n, L = P.L;
 
     // TMA writes need 128-byte aligned shared destinations
@@ -155,6 +169,24 @@ __global__ void __launch_bounds__(TX *TYT)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int q = tid; q < kMaxClasses; q += NT) sC[q] = P2{P.ctab[2 * q], P.ctab[2 * q + 1]};
+    if (HPX) {
+        for (int q = tid; q < 6 * BX; q += NT) {
+            const int k = q / BX, gi = i0 - XO + q % BX;
+            PX[q] = (P.prof[0] && gi >= 0 && gi <= P.nx) ? P.prof[0][k * NX1 + gi] : (T)0;
+        }
+    }
+    if (HPY) {
+        for (int q = tid; q < 6 * WY; q += NT) {
+            const int k = q / WY, gj = j0 - 1 + q % WY;
+            PY[q] = (P.prof[1] && gj >= 0 && gj <= P.ny) ? P.prof[1][k * NY1 + gj] : (T)0;
+        }
+    }
+    if (HPZ) {
+        for (int q = tid; q < 6 * ZMAX; q += NT) {
+            const int k = q / ZMAX, gp = kb - 1 + q % ZMAX;
+            PZ[q] = (P.prof[2] && gp >= 0 && gp <= P.nz) ? P.prof[2][k * (P.nz + 1) + gp] : (T)0;
+        }
+    }
     __syncthreads();
 
     // plane q lives in stage (q - kb + 1) mod 3; thread 0 tracks the parity of each stage's
@@ -163,9 +195,9 @@ __global__ void __launch_bounds__(TX *TYT)
         unsigned char *st = sm + s * Lay::STAGE;
         const uint32_t bar = bar0 + 8 * s;
         mbar_expect_tx(bar, Lay::TX_BYTES);
-        tma_load_4d(smem_u32(st), &tmF, i0 - XO, j0 - 1, q, 0, bar);
-        tma_load_4d(smem_u32(st + Lay::WIN_PAD), &tmF, i0 - XO, j0 - 1, q, 3, bar);
-        tma_load_4d(smem_u32(st + 2 * Lay::WIN_PAD), &tmC, i0, j0, q, 0, bar);
+        tma_load_4d(smem_u32(st), tmF, i0 - XO, j0 - 1, q, 0, bar);
+        tma_load_4d(smem_u32(st + Lay::WIN_PAD), tmF, i0 - XO, j0 - 1, q, 3, bar);
+        tma_load_4d(smem_u32(st + 2 * Lay::WIN_PAD), tmC, i0, j0, q, 0, bar);
     };
     uint32_t phase = 0;
     if (tid == 0) {
@@ -188,12 +220,13 @@ __global__ void __launch_bounds__(TX *TYT)
 
     // per-thread constants
     const bool col_live = i <= P.nx;
-    const int sx = slab_i(i, P.nx, n, P.lo[0], P.hi[0]);
+    const int sx = HPX ? slab_i(i, P.nx, n, P.lo[0], P.hi[0]) : -1;
+    const int lx = tx + XO;            // staged x-profile index of the own column
     int sy[CY];
     bool rlive[CY];
 #pragma unroll
     for (int r = 0; r < CY; ++r) {
-        sy[r] = slab_i(jb + r, P.ny, n, P.lo[1], P.hi[1]);
+        sy[r] = HPY ? slab_i(jb + r, P.ny, n, P.lo[1], P.hi[1]) : -1;
         rlive[r] = col_live && jb + r <= P.ny;
     }
     const int w0 = (ty * CY + 1) * BX + (tx + XO);   // window index of row r: w0 + r * BX
@@ -203,7 +236,7 @@ __global__ void __launch_bounds__(TX *TYT)
     // h_comp: 0 H_x, 1 H_y, 2 H_z, -1 none; h_live false stores a zero (outside the grid)
     constexpr int NHALO = 2 * TX + 2 * TY;
     static_assert(NHALO <= NT, "one halo value per thread");
-    int h_comp = -1, h_w = 0, h_i = 0, h_j = 0, h_sx = -1, h_sy = -1;
+    int h_comp = -1, h_w = 0, h_i = 0, h_j = 0, h_sx = -1, h_sy = -1, h_lx = 0, h_ly = 0;
     bool h_live = false;
     if (tid < NHALO) {
         if (tid < 2 * TX) {
@@ -212,6 +245,8 @@ __global__ void __launch_bounds__(TX *TYT)
             h_w = e + XO;
             h_i = i0 + e;
             h_j = j0 - 1;
+            h_lx = e + XO;
+            h_ly = 0;
             h_live = j0 > 0 && h_i <= P.nx;
         } else {
             const int e = tid - 2 * TX;
@@ -220,13 +255,67 @@ __global__ void __launch_bounds__(TX *TYT)
             h_w = (r + 1) * BX + (XO - 1);
             h_i = i0 - 1;
             h_j = j0 + r;
+            h_lx = XO - 1;
+            h_ly = r + 1;
             h_live = i0 > 0 && h_j <= P.ny;
         }
-        if (h_live) {
-            h_sx = slab_i(h_i, P.nx, n, P.lo[0], P.hi[0]);
-            h_sy = slab_i(h_j, P.ny, n, P.lo[1], P.hi[1]);
-        }
+        if (HPX && h_live) h_sx = slab_i(h_i, P.nx, n, P.lo[0], P.hi[0]);
+        if (HPY && h_live) h_sy = slab_i(h_j, P.ny, n, P.lo[1], P.hi[1]);
     }
+
+    // CPML auxiliaries of plane q for the own rows (pv) and the halo value (hv):
+    //   pv[r][0..3]  y slab: H_x, H_z, E_x, E_z    offset (q L + sy) px + i
+    //   pv[r][4..7]  z slab: H_x, H_y, E_x, E_y    offset (sz NY1 + j) px + i
+    //   pv[r][8..11] x slab: H_y, H_z, E_y, E_z    offset (q NY1 + j) L + sx
+    // fetched one plane ahead; the H values come from the read copy, the E values are the
+    // thread's own (updated in place by this thread only)
+    T pv[CY][12];
+    T hv[2] = {0, 0};
+    auto fetch = [&](int q) {
+        if (!HP || q < 0 || q > P.nz) return;
+        const int szq = HPZ ? slab_i(q, P.nz, n, P.lo[2], P.hi[2]) : -1;
+#pragma unroll
+        for (int r = 0; r < CY; ++r) {
+            const int j = jb + r;
+            if (!rlive[r]) continue;
+            if (HPY && sy[r] >= 0) {
+                const int o = (q * L + sy[r]) * px + i;
+                pv[r][0] = P.psiHr[1][0][o]; pv[r][1] = P.psiHr[1][1][o];
+                pv[r][2] = P.psiE[1][0][o];  pv[r][3] = P.psiE[1][1][o];
+            }
+            if (HPZ && szq >= 0) {
+                const int o = (szq * NY1 + j) * px + i;
+                pv[r][4] = P.psiHr[2][0][o]; pv[r][5] = P.psiHr[2][1][o];
+                pv[r][6] = P.psiE[2][0][o];  pv[r][7] = P.psiE[2][1][o];
+            }
+            if (HPX && sx >= 0) {
+                const int o = (q * NY1 + j) * L + sx;
+                pv[r][8] = P.psiHr[0][0][o];  pv[r][9] = P.psiHr[0][1][o];
+                pv[r][10] = P.psiE[0][0][o];  pv[r][11] = P.psiE[0][1][o];
+            }
+        }
+        if (h_live && q >= kb) {
+            // the two terms of the halo value: (first derivative, second derivative)
+            const int ys = h_sy >= 0 ? (q * L + h_sy) * px + h_i : 0;
+            const int zs = szq >= 0 ? (szq * NY1 + h_j) * px + h_i : 0;
+            const int xs = h_sx >= 0 ? (q * NY1 + h_j) * L + h_sx : 0;
+            if (h_comp == 0) {          // H_x: y then z
+                if (h_sy >= 0) hv[0] = P.psiHr[1][0][ys];
+                if (szq >= 0) hv[1] = P.psiHr[2][0][zs];
+            } else if (h_comp == 1) {   // H_y: z then x
+                if (szq >= 0) hv[0] = P.psiHr[2][1][zs];
+                if (h_sx >= 0) hv[1] = P.psiHr[0][0][xs];
+            } else {                    // H_z: x then y
+                if (h_sx >= 0) hv[0] = P.psiHr[0][1][xs];
+                if (h_sy >= 0) hv[1] = P.psiHr[1][1][ys];
+            }
+        }
+    };
+#pragma unroll
+    for (int r = 0; r < CY; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pv[r][k] = 0;
+    fetch(kb - 1);
 
     T hx_prev[CY], hy_prev[CY];
 #pragma unroll
@@ -245,7 +334,8 @@ __global__ void __launch_bounds__(TX *TYT)
         const uint8_t *cl = stp + 2 * Lay::WIN_PAD;
         const T *ex1 = reinterpret_cast<const T *>(stn), *ey1 = ex1 + WN;
         const bool pin = p >= 0;
-        const int sz = pin ? slab_i(p, P.nz, n, P.lo[2], P.hi[2]) : -1;
+        const int sz = (HPZ && pin) ? slab_i(p, P.nz, n, P.lo[2], P.hi[2]) : -1;
+        const int lz = p - kb + 1;   // staged z-profile index of plane p
 
         // E^n of this thread's rows (plus the row above for the y differences)
         T exv[CY + 1], ezv[CY + 1], eyv[CY], eyx[CY], ezx[CY], ey1v[CY], ex1v[CY];
@@ -269,15 +359,15 @@ __global__ void __launch_bounds__(TX *TYT)
             if (pin && p < P.nz) {
 #pragma unroll
                 for (int r = 0; r < CY; ++r) {
-                    const int w = w0 + r * BX, j = jb + r;
+                    const int w = w0 + r * BX, ly = ty * CY + r + 1;
                     T d1 = (ezv[r + 1] - ezv[r]) * P.rdy, d2 = (ey1v[r] - eyv[r]) * P.rdz;
-                    if (HP && sy[r] >= 0) d1 = read_term(d1, P.psiHr[1][0], ((long)p * L + sy[r]) * px + i, P.prof[1], NY1, j);
-                    if (HP && sz >= 0) d2 = read_term(d2, P.psiHr[2][0], ((long)sz * NY1 + j) * px + i, P.prof[2], NZ1, p);
+                    if (HPY && sy[r] >= 0) d1 = cpt(d1, pv[r][0], (T *)nullptr, PY, WY, 3, ly);
+                    if (HPZ && sz >= 0) d2 = cpt(d2, pv[r][4], (T *)nullptr, PZ, ZMAX, 3, lz);
                     hx_prev[r] = hox[w] - P.db * (d1 - d2);
                     d1 = (ex1v[r] - exv[r]) * P.rdz;
                     d2 = (ezx[r] - ezv[r]) * P.rdx;
-                    if (HP && sz >= 0) d1 = read_term(d1, P.psiHr[2][1], ((long)sz * NY1 + j) * px + i, P.prof[2], NZ1, p);
-                    if (HP && sx >= 0) d2 = read_term(d2, P.psiHr[0][0], ((long)p * NY1 + j) * L + sx, P.prof[0], NX1, i);
+                    if (HPZ && sz >= 0) d1 = cpt(d1, pv[r][5], (T *)nullptr, PZ, ZMAX, 3, lz);
+                    if (HPX && sx >= 0) d2 = cpt(d2, pv[r][8], (T *)nullptr, PX, BX, 3, lx);
                     hy_prev[r] = hoy[w] - P.db * (d1 - d2);
                 }
             }
@@ -286,44 +376,32 @@ __global__ void __launch_bounds__(TX *TYT)
             T hx[CY], hy[CY], hz[CY];
 #pragma unroll
             for (int r = 0; r < CY; ++r) {
-                const int w = w0 + r * BX, j = jb + r;
+                const int w = w0 + r * BX, j = jb + r, ly = ty * CY + r + 1;
                 const bool vx = rlive[r] && j < P.ny && p < P.nz;
                 const bool vy = rlive[r] && i < P.nx && p < P.nz;
                 const bool vz = rlive[r] && i < P.nx && j < P.ny;
                 // H_x(i, j+1/2, p+1/2) -= dt/mu0 (dEz/dy - dEy/dz)
                 T d1 = (ezv[r + 1] - ezv[r]) * P.rdy, d2 = (ey1v[r] - eyv[r]) * P.rdz;
-                if (HP && sy[r] >= 0) {
-                    const long o = ((long)p * L + sy[r]) * px + i;
-                    d1 = cpml_x(d1, P.psiHr[1][0] + o, vx ? P.psiHw[1][0] + o : (T *)nullptr, P.prof[1], NY1, 3, j);
-                }
-                if (HP && sz >= 0) {
-                    const long o = ((long)sz * NY1 + j) * px + i;
-                    d2 = cpml_x(d2, P.psiHr[2][0] + o, vx ? P.psiHw[2][0] + o : (T *)nullptr, P.prof[2], NZ1, 3, p);
-                }
+                if (HPY && sy[r] >= 0)
+                    d1 = cpt(d1, pv[r][0], vx ? P.psiHw[1][0] + (p * L + sy[r]) * px + i : (T *)nullptr, PY, WY, 3, ly);
+                if (HPZ && sz >= 0)
+                    d2 = cpt(d2, pv[r][4], vx ? P.psiHw[2][0] + (sz * NY1 + j) * px + i : (T *)nullptr, PZ, ZMAX, 3, lz);
                 hx[r] = hox[w] - P.db * (d1 - d2);
                 // H_y(i+1/2, j, p+1/2) -= dt/mu0 (dEx/dz - dEz/dx)
                 d1 = (ex1v[r] - exv[r]) * P.rdz;
                 d2 = (ezx[r] - ezv[r]) * P.rdx;
-                if (HP && sz >= 0) {
-                    const long o = ((long)sz * NY1 + j) * px + i;
-                    d1 = cpml_x(d1, P.psiHr[2][1] + o, vy ? P.psiHw[2][1] + o : (T *)nullptr, P.prof[2], NZ1, 3, p);
-                }
-                if (HP && sx >= 0) {
-                    const long o = ((long)p * NY1 + j) * L + sx;
-                    d2 = cpml_x(d2, P.psiHr[0][0] + o, vy ? P.psiHw[0][0] + o : (T *)nullptr, P.prof[0], NX1, 3, i);
-                }
+                if (HPZ && sz >= 0)
+                    d1 = cpt(d1, pv[r][5], vy ? P.psiHw[2][1] + (sz * NY1 + j) * px + i : (T *)nullptr, PZ, ZMAX, 3, lz);
+                if (HPX && sx >= 0)
+                    d2 = cpt(d2, pv[r][8], vy ? P.psiHw[0][0] + (p * NY1 + j) * L + sx : (T *)nullptr, PX, BX, 3, lx);
                 hy[r] = hoy[w] - P.db * (d1 - d2);
                 // H_z(i+1/2, j+1/2, p) -= dt/mu0 (dEy/dx - dEx/dy)
                 d1 = (eyx[r] - eyv[r]) * P.rdx;
                 d2 = (exv[r + 1] - exv[r]) * P.rdy;
-                if (HP && sx >= 0) {
-                    const long o = ((long)p * NY1 + j) * L + sx;
-                    d1 = cpml_x(d1, P.psiHr[0][1] + o, vz ? P.psiHw[0][1] + o : (T *)nullptr, P.prof[0], NX1, 3, i);
-                }
-                if (HP && sy[r] >= 0) {
-                    const long o = ((long)p * L + sy[r]) * px + i;
-                    d2 = cpml_x(d2, P.psiHr[1][1] + o, vz ? P.psiHw[1][1] + o : (T *)nullptr, P.prof[1], NY1, 3, j);
-                }
+                if (HPX && sx >= 0)
+                    d1 = cpt(d1, pv[r][9], vz ? P.psiHw[0][1] + (p * NY1 + j) * L + sx : (T *)nullptr, PX, BX, 3, lx);
+                if (HPY && sy[r] >= 0)
+                    d2 = cpt(d2, pv[r][1], vz ? P.psiHw[1][1] + (p * L + sy[r]) * px + i : (T *)nullptr, PY, WY, 3, ly);
                 hz[r] = hoz[w] - P.db * (d1 - d2);
                 sHn[w] = hx[r];
                 sHn[WN + w] = hy[r];
@@ -339,18 +417,18 @@ __global__ void __launch_bounds__(TX *TYT)
                     const int w = h_w;
                     if (h_comp == 0) {
                         T d1 = (ez0[w + BX] - ez0[w]) * P.rdy, d2 = (ey1[w] - ey0[w]) * P.rdz;
-                        if (HP && h_sy >= 0) d1 = read_term(d1, P.psiHr[1][0], ((long)p * L + h_sy) * px + h_i, P.prof[1], NY1, h_j);
-                        if (HP && sz >= 0) d2 = read_term(d2, P.psiHr[2][0], ((long)sz * NY1 + h_j) * px + h_i, P.prof[2], NZ1, p);
+                        if (HPY && h_sy >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PY, WY, 3, h_ly);
+                        if (HPZ && sz >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PZ, ZMAX, 3, lz);
                         v = hox[w] - P.db * (d1 - d2);
                     } else if (h_comp == 1) {
                         T d1 = (ex1[w] - ex0[w]) * P.rdz, d2 = (ez0[w + 1] - ez0[w]) * P.rdx;
-                        if (HP && sz >= 0) d1 = read_term(d1, P.psiHr[2][1], ((long)sz * NY1 + h_j) * px + h_i, P.prof[2], NZ1, p);
-                        if (HP && h_sx >= 0) d2 = read_term(d2, P.psiHr[0][0], ((long)p * NY1 + h_j) * L + h_sx, P.prof[0], NX1, h_i);
+                        if (HPZ && sz >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PZ, ZMAX, 3, lz);
+                        if (HPX && h_sx >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PX, BX, 3, h_lx);
                         v = hoy[w] - P.db * (d1 - d2);
                     } else {
                         T d1 = (ey0[w + 1] - ey0[w]) * P.rdx, d2 = (ex0[w + BX] - ex0[w]) * P.rdy;
-                        if (HP && h_sx >= 0) d1 = read_term(d1, P.psiHr[0][1], ((long)p * NY1 + h_j) * L + h_sx, P.prof[0], NX1, h_i);
-                        if (HP && h_sy >= 0) d2 = read_term(d2, P.psiHr[1][1], ((long)p * L + h_sy) * px + h_i, P.prof[1], NY1, h_j);
+                        if (HPX && h_sx >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PX, BX, 3, h_lx);
+                        if (HPY && h_sy >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PY, WY, 3, h_ly);
                         v = hoz[w] - P.db * (d1 - d2);
                     }
                 }
@@ -362,48 +440,30 @@ __global__ void __launch_bounds__(TX *TYT)
             T hz_up = shz[w0 - BX], hx_up = shx[w0 - BX];
 #pragma unroll
             for (int r = 0; r < CY; ++r) {
-                const int w = w0 + r * BX, j = jb + r;
+                const int w = w0 + r * BX, j = jb + r, ly = ty * CY + r + 1;
                 const int crow = (ty * CY + r) * TX + tx;
                 T exn = 0, eyn = 0, ezn = 0;
                 int c = cl[crow];
                 if (c) {   // E_x(i+1/2, j, p) = Ca E_x + Cb (dHz/dy - dHy/dz)
                     T d1 = (hz[r] - hz_up) * P.rdy, d2 = (hy[r] - hy_prev[r]) * P.rdz;
-                    if (HP && sy[r] >= 0) {
-                        T *o = P.psiE[1][0] + ((long)p * L + sy[r]) * px + i;
-                        d1 = cpml_x(d1, o, o, P.prof[1], NY1, 0, j);
-                    }
-                    if (HP && sz >= 0) {
-                        T *o = P.psiE[2][0] + ((long)sz * NY1 + j) * px + i;
-                        d2 = cpml_x(d2, o, o, P.prof[2], NZ1, 0, p);
-                    }
+                    if (HPY && sy[r] >= 0) d1 = cpt(d1, pv[r][2], P.psiE[1][0] + (p * L + sy[r]) * px + i, PY, WY, 0, ly);
+                    if (HPZ && sz >= 0) d2 = cpt(d2, pv[r][6], P.psiE[2][0] + (sz * NY1 + j) * px + i, PZ, ZMAX, 0, lz);
                     const P2 k = sC[c];
                     exn = k.x * exv[r] + k.y * (d1 - d2);
                 }
                 c = cl[TX * TY + crow];
                 if (c) {   // E_y(i, j+1/2, p) = Ca E_y + Cb (dHx/dz - dHz/dx)
                     T d1 = (hx[r] - hx_prev[r]) * P.rdz, d2 = (hz[r] - shz[w - 1]) * P.rdx;
-                    if (HP && sz >= 0) {
-                        T *o = P.psiE[2][1] + ((long)sz * NY1 + j) * px + i;
-                        d1 = cpml_x(d1, o, o, P.prof[2], NZ1, 0, p);
-                    }
-                    if (HP && sx >= 0) {
-                        T *o = P.psiE[0][0] + ((long)p * NY1 + j) * L + sx;
-                        d2 = cpml_x(d2, o, o, P.prof[0], NX1, 0, i);
-                    }
+                    if (HPZ && sz >= 0) d1 = cpt(d1, pv[r][7], P.psiE[2][1] + (sz * NY1 + j) * px + i, PZ, ZMAX, 0, lz);
+                    if (HPX && sx >= 0) d2 = cpt(d2, pv[r][10], P.psiE[0][0] + (p * NY1 + j) * L + sx, PX, BX, 0, lx);
                     const P2 k = sC[c];
                     eyn = k.x * eyv[r] + k.y * (d1 - d2);
                 }
                 c = cl[2 * TX * TY + crow];
                 if (c) {   // E_z(i, j, p+1/2) = Ca E_z + Cb (dHy/dx - dHx/dy)
                     T d1 = (hy[r] - shy[w - 1]) * P.rdx, d2 = (hx[r] - hx_up) * P.rdy;
-                    if (HP && sx >= 0) {
-                        T *o = P.psiE[0][1] + ((long)p * NY1 + j) * L + sx;
-                        d1 = cpml_x(d1, o, o, P.prof[0], NX1, 0, i);
-                    }
-                    if (HP && sy[r] >= 0) {
-                        T *o = P.psiE[1][1] + ((long)p * L + sy[r]) * px + i;
-                        d2 = cpml_x(d2, o, o, P.prof[1], NY1, 0, j);
-                    }
+                    if (HPX && sx >= 0) d1 = cpt(d1, pv[r][11], P.psiE[0][1] + (p * NY1 + j) * L + sx, PX, BX, 0, lx);
+                    if (HPY && sy[r] >= 0) d2 = cpt(d2, pv[r][3], P.psiE[1][1] + (p * L + sy[r]) * px + i, PY, WY, 0, ly);
                     const P2 k = sC[c];
                     ezn = k.x * ezv[r] + k.y * (d1 - d2);
                 }
@@ -419,6 +479,8 @@ __global__ void __launch_bounds__(TX *TYT)
                 hy_prev[r] = hy[r];
             }
         }
+        // auxiliaries of the next plane, in flight during the barrier and the next wait
+        fetch(p + 1);
         // every thread is done with stage sp: refill it with plane p + 3
         __syncthreads();
         if (tid == 0 && p + 3 <= ke + 1) {
@@ -430,77 +492,85 @@ __global__ void __launch_bounds__(TX *TYT)
     }
 }
 
-// one launch over tiles [tx0, tx1) x [ty0, ty1) and planes z0..z1
-template <typename T, int TX, int TYT, int CY, bool HP>
-cudaError_t launch_box(FusedArgs<T> a, const CUtensorMap &tmF, const CUtensorMap &tmC, int *status,
-                       cudaStream_t s, int tx0, int tx1, int ty0, int ty1, int z0, int z1)
+// Block b takes work item b (instance, tile origin, z-segment); the instance's arguments for
+// the current buffer parity are copied to shared memory behind the TMA layout.
+template <typename T, int TX, int TYT, int CY, int PM>
+__global__ void __launch_bounds__(TX *TYT)
+    k_yee_tma_batch(const BatchItem *items, const FusedArgs<T> *args, const CUtensorMap *maps,
+                    int parity, int *status)
 {
+    extern __shared__ __align__(128) unsigned char sm[];
     using Lay = TmaLayout<T, TX, TYT * CY>;
-    if (tx1 <= tx0 || ty1 <= ty0 || z1 < z0) return cudaSuccess;
-    a.tx0 = tx0; a.ty0 = ty0; a.z0 = z0; a.z1 = z1;
-    dim3 blk(TX, TYT), grd(tx1 - tx0, ty1 - ty0, (z1 - z0 + 1 + a.kseg - 1) / a.kseg);
-    k_yee_tma<T, TX, TYT, CY, HP><<<grd, blk, Lay::BYTES, s>>>(a, tmF, tmC, status);
+    static_assert(Lay::BYTES % 16 == 0, "argument copy alignment");
+    const BatchItem it = items[blockIdx.x];
+    FusedArgs<T> *sP = reinterpret_cast<FusedArgs<T> *>(sm + Lay::BYTES);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int *src = reinterpret_cast<const int *>(args + 2 * it.inst + parity);
+    int *dst = reinterpret_cast<int *>(sP);
+    for (int q = tid; q < (int)(sizeof(FusedArgs<T>) / 4); q += TX * TYT) dst[q] = src[q];
+    __syncthreads();
+    const CUtensorMap *m = maps + 2 * (2 * it.inst + parity);
+    tma_tile<T, TX, TYT, CY, PM>(*sP, m, m + 1, status, sm, it.i0, it.j0, it.kb, it.ke);
+}
+
+template <typename T, int TX, int TYT, int CY, int PM>
+int batch_bytes()
+{
+    return TmaLayout<T, TX, TYT * CY>::BYTES + (int)sizeof(FusedArgs<T>);
+}
+
+template <typename T, int TX, int TYT, int CY, int PM>
+cudaError_t prep_one()
+{
+    return cudaFuncSetAttribute(k_yee_tma_batch<T, TX, TYT, CY, PM>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                batch_bytes<T, TX, TYT, CY, PM>());
+}
+
+template <typename T, int TX, int TYT, int CY>
+cudaError_t prep_kinds()
+{
+    cudaError_t e;
+    if ((e = prep_one<T, TX, TYT, CY, 0>()) != cudaSuccess) return e;
+    if ((e = prep_one<T, TX, TYT, CY, 1>()) != cudaSuccess) return e;
+    if ((e = prep_one<T, TX, TYT, CY, 2>()) != cudaSuccess) return e;
+    if ((e = prep_one<T, TX, TYT, CY, 4>()) != cudaSuccess) return e;
+    return prep_one<T, TX, TYT, CY, 7>();
+}
+
+template <typename T, int TX, int TYT, int CY, int PM>
+cudaError_t launch_kind(const TmaPlan &pl, int kind, int parity, int *status, cudaStream_t s)
+{
+    const int cnt = pl.count[kind];
+    if (cnt <= 0) return cudaSuccess;
+    k_yee_tma_batch<T, TX, TYT, CY, PM><<<cnt, dim3(TX, TYT), batch_bytes<T, TX, TYT, CY, PM>(), s>>>(
+        pl.items + pl.offset[kind], (const FusedArgs<T> *)pl.args, pl.maps, parity, status);
     return cudaGetLastError();
 }
 
-// The instantiation without CPML code (about half the registers) covers the box of tiles and
-// planes whose nodes, halo nodes and warm-up plane touch no absorbing slab; the CPML
-// instantiation covers the frame around it (at most six boxes).  Every launch reads buffer A
-// and writes a disjoint part of buffer B.
 template <typename T, int TX, int TYT, int CY>
-cudaError_t launch_tma_t(const FusedArgs<T> &a, const CUtensorMap &tmF, const CUtensorMap &tmC,
-                         int *status, cudaStream_t s, const SideStream *side)
+cudaError_t launch_plan_t(const TmaPlan &pl, int parity, int *status, cudaStream_t s,
+                          const SideStream *side)
 {
-    constexpr int TY = TYT * CY;
-    const int ntx = (a.nx + 1 + TX - 1) / TX, nty = (a.ny + 1 + TY - 1) / TY, nz = a.nz, n = a.n;
-    const bool hp = n > 0 && (a.lo[0] || a.hi[0] || a.lo[1] || a.hi[1] || a.lo[2] || a.hi[2]);
-    if (!hp) return launch_box<T, TX, TYT, CY, false>(a, tmF, tmC, status, s, 0, ntx, 0, nty, 0, nz);
-    // interior: halo column i0-1 >= n and last node i0+TX-1 < nx-n (same in y); planes from
-    // the warm-up plane on stay outside the z slabs
-    auto lo_tile = [](int on, int n_, int tile) { return on ? (n_ + 1 + tile - 1) / tile : 0; };
-    auto hi_tile = [](int on, int N, int n_, int tile, int count) {
-        if (!on) return count;
-        const int lim = N - n_ - tile;   // largest i0 with i0 + tile - 1 < N - n
-        return lim < 0 ? 0 : lim / tile + 1;
-    };
-    const int txa = lo_tile(a.lo[0], n, TX), txb = min(ntx, hi_tile(a.hi[0], a.nx, n, TX, ntx));
-    const int tya = lo_tile(a.lo[1], n, TY), tyb = min(nty, hi_tile(a.hi[1], a.ny, n, TY, nty));
-    const int za = a.lo[2] ? n + 1 : 0, zb = a.hi[2] ? nz - n - 1 : nz;
-    if (txa >= txb || tya >= tyb || za > zb)
-        return launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, s, 0, ntx, 0, nty, 0, nz);
-    // the frame (latency-bound CPML work) runs on a side stream next to the interior
-    // (bandwidth-bound), joined back before the step's epilogue
+    // kind 0 (no CPML) on the main stream; the CPML kinds on the side stream next to it
     cudaError_t e;
+    const bool frame = pl.count[1] + pl.count[2] + pl.count[3] + pl.count[4] > 0;
     cudaStream_t fs = s;
-    if (side && side->stream) {
+    if (frame && side && side->stream) {
         if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
         fs = side->stream;
     }
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, 0, ntx, 0, nty, zb + 1, nz)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, 0, txa, 0, nty, za, zb)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, txb, ntx, 0, nty, za, zb)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, txa, txb, 0, tya, za, zb)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, txa, txb, tyb, nty, za, zb)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, true>(a, tmF, tmC, status, fs, 0, ntx, 0, nty, 0, za - 1)) != cudaSuccess) return e;
-    if ((e = launch_box<T, TX, TYT, CY, false>(a, tmF, tmC, status, s, txa, txb, tya, tyb, za, zb)) != cudaSuccess) return e;
+    if ((e = launch_kind<T, TX, TYT, CY, 7>(pl, 4, parity, status, fs)) != cudaSuccess) return e;
+    if ((e = launch_kind<T, TX, TYT, CY, 1>(pl, 1, parity, status, fs)) != cudaSuccess) return e;
+    if ((e = launch_kind<T, TX, TYT, CY, 2>(pl, 2, parity, status, fs)) != cudaSuccess) return e;
+    if ((e = launch_kind<T, TX, TYT, CY, 4>(pl, 3, parity, status, fs)) != cudaSuccess) return e;
+    if ((e = launch_kind<T, TX, TYT, CY, 0>(pl, 0, parity, status, s)) != cudaSuccess) return e;
     if (fs != s) {
         if ((e = cudaEventRecord(side->join, fs)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-template <typename T, int TX, int TYT, int CY>
-cudaError_t prepare_t()
-{
-    cudaError_t e = cudaFuncSetAttribute(k_yee_tma<T, TX, TYT, CY, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TmaLayout<T, TX, TYT * CY>::BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_yee_tma<T, TX, TYT, CY, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TmaLayout<T, TX, TYT * CY>::BYTES);
 }
 
 }  // namespace
@@ -512,33 +582,78 @@ int tma_box_x(int tile_x) { return tile_x + 2 * (16 / (int)sizeof(T)); }
 cudaError_t tma_prepare()
 {
     cudaError_t e;
-    if ((e = prepare_t<float, 32, 4, 1>()) != cudaSuccess) return e;
-    if ((e = prepare_t<float, 32, 8, 1>()) != cudaSuccess) return e;
-    if ((e = prepare_t<float, 32, 8, 2>()) != cudaSuccess) return e;
-    if ((e = prepare_t<double, 32, 4, 1>()) != cudaSuccess) return e;
-    if ((e = prepare_t<double, 32, 8, 1>()) != cudaSuccess) return e;
-    return prepare_t<double, 32, 8, 2>();
+    if ((e = prep_kinds<float, 32, 4, 1>()) != cudaSuccess) return e;
+    if ((e = prep_kinds<float, 32, 8, 1>()) != cudaSuccess) return e;
+    if ((e = prep_kinds<float, 32, 8, 2>()) != cudaSuccess) return e;
+    if ((e = prep_kinds<double, 32, 4, 1>()) != cudaSuccess) return e;
+    if ((e = prep_kinds<double, 32, 8, 1>()) != cudaSuccess) return e;
+    return prep_kinds<double, 32, 8, 2>();
 }
 
 // tile_y = rows per block: 4 -> 4 threads x 1 row, 8 -> 8 x 1, 16 -> 8 x 2
 template <typename T>
-cudaError_t launch_tma(const FusedArgs<T> &a, const CUtensorMap &tmF, const CUtensorMap &tmC,
-                       int tile_y, int *status, cudaStream_t s, const SideStream *side)
+cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *status, cudaStream_t s,
+                            const SideStream *side)
 {
     switch (tile_y) {
-    case 4: return launch_tma_t<T, 32, 4, 1>(a, tmF, tmC, status, s, side);
-    case 16: return launch_tma_t<T, 32, 8, 2>(a, tmF, tmC, status, s, side);
-    default: return launch_tma_t<T, 32, 8, 1>(a, tmF, tmC, status, s, side);
+    case 4: return launch_plan_t<T, 32, 4, 1>(pl, parity, status, s, side);
+    case 16: return launch_plan_t<T, 32, 8, 2>(pl, parity, status, s, side);
+    default: return launch_plan_t<T, 32, 8, 1>(pl, parity, status, s, side);
+    }
+}
+
+// Work items of one grid for tile height tile_y.  The interior box (tiles whose nodes and halo
+// nodes avoid the x and y slabs, planes from the warm-up plane on outside the z slabs) is kind
+// 0; tiles outside it in x only -> kind 1 (x CPML), in y only -> kind 2, in z only -> kind 3
+// (z CPML), anything else -> kind 4 (all CPML).  z segments never straddle the z-slab limits.
+void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
+               const int hi[3], std::vector<BatchItem> items[5])
+{
+    const int TX = 32, TY = tile_y;
+    const int ntx = (nx + 1 + TX - 1) / TX, nty = (ny + 1 + TY - 1) / TY;
+    const bool hp = n > 0 && (lo[0] || hi[0] || lo[1] || hi[1] || lo[2] || hi[2]);
+    auto lo_tile = [](int on, int n_, int tile) { return on ? (n_ + 1 + tile - 1) / tile : 0; };
+    auto hi_tile = [](int on, int N, int n_, int tile, int count) {
+        if (!on) return count;
+        const int lim = N - n_ - tile;   // largest origin with origin + tile - 1 < N - n
+        return lim < 0 ? 0 : lim / tile + 1;
+    };
+    int txa = 0, txb = ntx, tya = 0, tyb = nty, za = 0, zb = nz;
+    if (hp) {
+        txa = lo_tile(lo[0] && n > 0, n, TX); txb = std::min(ntx, hi_tile(hi[0] && n > 0, nx, n, TX, ntx));
+        tya = lo_tile(lo[1] && n > 0, n, TY); tyb = std::min(nty, hi_tile(hi[1] && n > 0, ny, n, TY, nty));
+        za = lo[2] ? n + 1 : 0;
+        zb = hi[2] ? nz - n - 1 : nz;
+    }
+    // z segments (the same for every tile of the grid), outermost, so that blocks launched
+    // together are x/y neighbours on the same planes and share halo rows through L2
+    std::vector<std::pair<int, int>> segs;
+    for (int k = 0; k <= nz;) {
+        const bool inz = k >= za && k <= zb;
+        const int stop = inz ? zb : (k < za ? za - 1 : nz);
+        const int kend = std::min(stop, k + kseg - 1);
+        segs.push_back({k, kend});
+        k = kend + 1;
+    }
+    for (const auto &sg : segs) {
+        const bool inz = sg.first >= za && sg.first <= zb;
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                const bool inx = tx >= txa && tx < txb, iny = ty >= tya && ty < tyb;
+                int kind;
+                if (!hp) kind = 0;
+                else if (inz) kind = inx ? (iny ? 0 : 2) : (iny ? 1 : 4);
+                else kind = (inx && iny) ? 3 : 4;
+                items[kind].push_back(BatchItem{inst, tx * TX, ty * TY, sg.first, sg.second});
+            }
     }
 }
 
 template int tma_box_x<float>(int);
 template int tma_box_x<double>(int);
-template cudaError_t launch_tma<float>(const FusedArgs<float> &, const CUtensorMap &,
-                                       const CUtensorMap &, int, int *, cudaStream_t,
-                                       const SideStream *);
-template cudaError_t launch_tma<double>(const FusedArgs<double> &, const CUtensorMap &,
-                                        const CUtensorMap &, int, int *, cudaStream_t,
-                                        const SideStream *);
+template cudaError_t launch_tma_plan<float>(const TmaPlan &, int, int, int *, cudaStream_t,
+                                            const SideStream *);
+template cudaError_t launch_tma_plan<double>(const TmaPlan &, int, int, int *, cudaStream_t,
+                                             const SideStream *);
 
 }  // namespace yf

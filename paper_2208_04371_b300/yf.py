@@ -58,6 +58,20 @@ class PortDfts(C.Structure):
                 ("I_re", C.POINTER(C.c_double)), ("I_im", C.POINTER(C.c_double))]
 
 
+class InstanceDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("dy", C.c_double), ("dz", C.c_double), ("ids", C.c_void_p), ("nmat", C.c_int),
+                ("eps_r", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("mu_r", C.POINTER(C.c_double)), ("is_pec", C.c_void_p), ("nsheets", C.c_int),
+                ("sheets", C.POINTER(C.c_int)), ("bc", C.c_int * 6), ("pml_cells", C.c_int),
+                ("pml_order", C.c_int), ("pml_sigma_scale", C.c_double),
+                ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
+                ("src_plane", C.c_int), ("src_j0", C.c_int), ("src_j1", C.c_int),
+                ("src_k0", C.c_int), ("src_k1", C.c_int), ("src", Waveform), ("nports", C.c_int),
+                ("ports", C.POINTER(PortDesc)), ("nfreq", C.c_int),
+                ("freqs", C.POINTER(C.c_double))]
+
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _i = C.c_int
@@ -90,6 +104,16 @@ _SIGS = {
     "yf_set_variant": (_i, [_vp, _i, _i, _i]),
     "yf_profile_steps": (_i, [_vp, C.c_long, _dp, C.POINTER(_i)]),
     "yf_kernel_name": (C.c_char_p, [_vp, _i]),
+    "yf_autotune": (_i, [_vp, C.c_char_p, _i, C.POINTER(_i), C.POINTER(_i)]),
+    "yf_batch_autotune": (_i, [_vp, C.c_char_p, _i, C.POINTER(_i), C.POINTER(_i)]),
+    "yf_batch_create": (_i, [_i, C.POINTER(InstanceDesc), _d, _i, _vp, C.POINTER(_vp)]),
+    "yf_batch_destroy": (_i, [_vp]),
+    "yf_batch_set_tiling": (_i, [_vp, _i, _i]),
+    "yf_batch_step": (_i, [_vp, C.c_long]),
+    "yf_batch_sync": (_i, [_vp]),
+    "yf_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_long), _dp, C.POINTER(C.c_long)]),
+    "yf_batch_grid": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "yf_batch_read_port_dft": (_i, [_vp, _i, _i, _i, _dp, _dp, _dp, _dp]),
     "yf_checkpoint_save": (_i, [_vp, C.c_char_p]),
     "yf_checkpoint_load": (_i, [_vp, C.c_char_p]),
 }
@@ -312,6 +336,14 @@ def set_variant(g, variant, tile_y=8, kseg=16):
     _check(_lib.yf_set_variant(C.c_void_p(g), variant, tile_y, kseg))
 
 
+def autotune(g, cache_path=None, reps=4):
+    """(tile_y, kseg) chosen for grid g (before its first step); state is reset to zero."""
+    ty, ks = C.c_int(), C.c_int()
+    _check(_lib.yf_autotune(C.c_void_p(g), cache_path.encode() if cache_path else None, reps,
+                            C.byref(ty), C.byref(ks)))
+    return ty.value, ks.value
+
+
 def reset(g):
     _check(_lib.yf_reset(C.c_void_p(g)))
 
@@ -413,6 +445,130 @@ class Grid:
     def close(self):
         if self.h is not None:
             grid_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- batched instances
+
+class Batch:
+    """Owns a yf_batch of workloads.Problem instances (one shared time step)."""
+
+    def __init__(self, probs, prec=FP32, stream=None, dt: float = 0.0, tile_y: int = 8,
+                 kseg: int = 16):
+        self.probs = list(probs)
+        n = len(self.probs)
+        descs = (InstanceDesc * n)()
+        self._keep = []
+        for q, p in enumerate(self.probs):
+            d = descs[q]
+            d.nx, d.ny, d.nz, d.dx, d.dy, d.dz = p.nx, p.ny, p.nz, p.dx, p.dy, p.dz
+            ids = np.ascontiguousarray(p.ids, dtype=np.uint8)
+            eps, ke = _f64(p.eps_r)
+            sig, ks = _f64(p.sigma)
+            mu, km = _f64(p.mu_r)
+            pec = np.ascontiguousarray(np.asarray(p.is_pec, dtype=np.uint8))
+            sh = np.ascontiguousarray(np.array(p.sheets, dtype=np.int32).reshape(-1, 6))
+            fr, kf = _f64(p.freqs)
+            ports = (PortDesc * max(1, len(p.ports)))()
+            for k, pt in enumerate(p.ports):
+                ports[k] = PortDesc(axis=0, plane=pt.plane, direction=pt.direction, j0=pt.j0,
+                                    j1=pt.j1, k0=pt.k0, k1=pt.k1, kb=pt.kb, kt=pt.kt,
+                                    margin=pt.margin, width=pt.width)
+            self._keep += [ids, ke, ks, km, pec, sh, kf, ports]
+            d.ids = C.c_void_p(ids.ctypes.data)
+            d.nmat = len(ke)
+            d.eps_r, d.sigma, d.mu_r = eps, sig, mu
+            d.is_pec = C.c_void_p(pec.ctypes.data)
+            d.nsheets = sh.shape[0]
+            d.sheets = sh.ctypes.data_as(C.POINTER(C.c_int))
+            for f in range(6):
+                d.bc[f] = int(p.bc[f])
+            d.pml_cells, d.pml_order = p.pml_cells, p.pml_order
+            d.pml_sigma_scale, d.pml_kappa_max, d.pml_alpha_max = (p.pml_sigma_scale,
+                                                                   p.pml_kappa_max,
+                                                                   p.pml_alpha_max)
+            s = p.source
+            d.src_plane, d.src_j0, d.src_j1, d.src_k0, d.src_k1 = s.plane, s.j0, s.j1, s.k0, s.k1
+            d.src = Waveform(kind=s.kind, amplitude=s.amplitude, p0=s.param0, p1=s.param1,
+                             t0=s.t0, table=None, table_len=0)
+            d.nports = len(p.ports)
+            d.ports = ports
+            d.nfreq = len(kf)
+            d.freqs = fr
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        _check(_lib.yf_batch_create(n, descs, dt, prec, st, C.byref(h)))
+        self.h = h.value
+        if (tile_y, kseg) != (8, 16):
+            _check(_lib.yf_batch_set_tiling(C.c_void_p(self.h), tile_y, kseg))
+        self._keep.append(descs)
+        cells = C.c_long()
+        dtv = C.c_double()
+        _check(_lib.yf_batch_info(C.c_void_p(self.h), None, C.byref(cells), C.byref(dtv), None))
+        self.cells, self.dt = cells.value, dtv.value
+
+    def set_tiling(self, tile_y, kseg):
+        _check(_lib.yf_batch_set_tiling(C.c_void_p(self.h), tile_y, kseg))
+
+    def autotune(self, cache_path=None, reps=3):
+        ty, ks = C.c_int(), C.c_int()
+        _check(_lib.yf_batch_autotune(C.c_void_p(self.h),
+                                      cache_path.encode() if cache_path else None, reps,
+                                      C.byref(ty), C.byref(ks)))
+        return ty.value, ks.value
+
+    def step(self, n):
+        _check(_lib.yf_batch_step(C.c_void_p(self.h), int(n)))
+
+    def sync(self):
+        _check(_lib.yf_batch_sync(C.c_void_p(self.h)))
+
+    def grid(self, inst) -> int:
+        g = C.c_void_p()
+        _check(_lib.yf_batch_grid(C.c_void_p(self.h), inst, C.byref(g)))
+        return g.value
+
+    def port_dfts(self, inst, kind=DFT_FP64):
+        p = self.probs[inst]
+        nf = len(p.freqs)
+        V = np.zeros((len(p.ports), nf), complex)
+        I = np.zeros((len(p.ports), nf), complex)
+        for q in range(len(p.ports)):
+            a = np.zeros((4, nf))
+            _check(_lib.yf_batch_read_port_dft(C.c_void_p(self.h), inst, q, kind,
+                                               *[a[r].ctypes.data_as(_dp) for r in range(4)]))
+            V[q], I[q] = a[0] + 1j * a[1], a[2] + 1j * a[3]
+        return V, I
+
+    def sparams(self, inst, z_ref=50.0):
+        return read_sparams(self.grid(inst), len(self.probs[inst].freqs), z_ref)
+
+    def fields(self, inst, prec=None) -> np.ndarray:
+        p = self.probs[inst]
+        dt_ = np.float32 if (prec or FP32) == FP32 else np.float64
+        out = np.zeros((6, p.nz + 1, p.ny + 1, p.nx + 1))
+        buf = np.zeros((p.nz + 1, p.ny + 1, p.nx + 1), dtype=dt_)
+        g = self.grid(inst)
+        for c in range(6):
+            read_fields(g, c, buf)
+            out[c] = buf
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.yf_batch_destroy(C.c_void_p(self.h))
             self.h = None
 
     def __enter__(self):
