@@ -240,6 +240,13 @@ yf_status yf_sparams_noalloc(int nports, int nfreq, const double *freqs, const d
 yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, double *Zr,
                           double *Zc, double *tau);
 
+/* yf_read_sparams from a chosen accumulator set (YF_DFT_FP64, YF_DFT_KAHAN32 or YF_DFT_FP32;
+ * YF_E_STATE if that set was not enabled by yf_set_dft_mode).  The extraction itself is FP64
+ * whichever accumulators fed it: this is how the precision study (FP32 fields, three DFT
+ * accumulator precisions, Sec. 2's running transform over a million steps) compares them. */
+yf_status yf_read_sparams_acc(yf_grid *g, int kind, double z_ref, double *S_star, double *S,
+                              double *Zr, double *Zc, double *tau);
+
 /* Start a new solve on the same grid: zero fields, CPML auxiliaries, DFT accumulators,
  * step count and error bits, and reopen the geometry (yf_set_materials and
  * yf_add_pec_sheet accept new input; sheets added before are dropped).  Boundaries,
@@ -251,6 +258,11 @@ yf_status yf_reset(yf_grid *g);
  * of a step (names via yf_kernel_name).  *nkern receives the number of kernels (<= 8). */
 yf_status yf_profile_steps(yf_grid *g, long n, double *ms_per_launch, int *nkern);
 const char *yf_kernel_name(yf_grid *g, int idx);
+
+/* Number of kernel launches one yf_step issues per time step with the current variant and
+ * tiling (the stencil launches plus the epilogue), for launch accounting.  Finalises the
+ * geometry like a first yf_step would. */
+yf_status yf_launches_per_step(yf_grid *g, int *n);
 
 /* Binary checkpoint of fields, CPML auxiliaries, DFT accumulators and the step count;
  * load requires a grid created and configured identically. */

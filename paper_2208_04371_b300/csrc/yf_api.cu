@@ -841,8 +841,8 @@ yf_status yf_read_port_dft(yf_grid *g, int port, int kind, double *V_re, double 
     return YF_OK;
 }
 
-yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, double *Zr,
-                          double *Zc, double *tau)
+yf_status yf_read_sparams_acc(yf_grid *g, int kind, double z_ref, double *S_star, double *S,
+                              double *Zr, double *Zc, double *tau)
 {
     if (!g) return fail(YF_E_INVALID, "yf_read_sparams: NULL grid");
     if (g->ports.size() != 2) return fail(YF_E_INVALID, "yf_read_sparams: needs exactly two ports");
@@ -853,11 +853,17 @@ yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, d
             return fail(YF_E_INVALID, "yf_read_sparams: ports differ in frequencies");
     std::vector<double> d(8 * (size_t)nf);
     for (int p = 0; p < 2; ++p) {
-        yf_status st = yf_read_port_dft(g, p, YF_DFT_FP64, &d[(4 * p + 0) * nf], &d[(4 * p + 1) * nf],
+        yf_status st = yf_read_port_dft(g, p, kind, &d[(4 * p + 0) * nf], &d[(4 * p + 1) * nf],
                                         &d[(4 * p + 2) * nf], &d[(4 * p + 3) * nf]);
         if (st != YF_OK) return st;
     }
     return sparams_uniform(nf, g->freqs.data(), d.data(), g->ports[1].dir, z_ref, S_star, S, Zr, Zc, tau);
+}
+
+yf_status yf_read_sparams(yf_grid *g, double z_ref, double *S_star, double *S, double *Zr,
+                          double *Zc, double *tau)
+{
+    return yf_read_sparams_acc(g, YF_DFT_FP64, z_ref, S_star, S, Zr, Zc, tau);
 }
 
 yf_status yf_reset(yf_grid *g)
@@ -936,13 +942,27 @@ const char *yf_kernel_name(yf_grid *g, int idx)
 {
     static const char *ref[] = {"k_update_h", "k_update_e", "k_epilogue"};
     static const char *fused[] = {"k_yee_fused", "k_epilogue"};
-    static const char *tma[] = {"k_yee_tma", "k_epilogue"};
+    static const char *tma[] = {"k_yee_tma_batch", "k_epilogue"};
     static const char *skew[] = {"k_yee_skew", "k_epilogue"};
     if (!g) return "";
     if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
     if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
     if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";
     return (idx >= 0 && idx < 3) ? ref[idx] : "";
+}
+
+yf_status yf_launches_per_step(yf_grid *g, int *n)
+{
+    if (!g || !n) return fail(YF_E_INVALID, "yf_launches_per_step: NULL argument");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    int k = 0;
+    if (g->variant == 0) k = 2;
+    else if (g->variant == 2)
+        for (int q = 0; q < 5; ++q) k += g->plan.count[q] > 0;
+    else k = 1;
+    *n = k + 1;
+    return YF_OK;
 }
 
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)

@@ -99,6 +99,8 @@ _SIGS = {
     "yf_sparams": (_i, [_i, _i, _dp, C.POINTER(PortDfts), C.POINTER(PortDfts), _d, _dp, _dp,
                         _dp, _dp, _dp]),
     "yf_read_sparams": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _dp]),
+    "yf_read_sparams_acc": (_i, [_vp, _i, _d, _dp, _dp, _dp, _dp, _dp]),
+    "yf_launches_per_step": (_i, [_vp, C.POINTER(_i)]),
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
     "yf_set_variant": (_i, [_vp, _i, _i, _i]),
@@ -321,13 +323,17 @@ def sparams_noalloc(nports, nfreq, freqs, V_inc, I_inc, V_tot, S, Zr, S_star=Non
                                    C.c_void_p(int(stream)) if stream else None))
 
 
-def read_sparams(g, nfreq, z_ref=50.0):
+def read_sparams(g, nfreq, z_ref=50.0, kind=DFT_FP64):
     ss, ssp = _cplx_out((nfreq, 2, 2))
     s, sp = _cplx_out((nfreq, 2, 2))
     zr, zrp = _cplx_out((2, nfreq))
     zc, zcp = _cplx_out((nfreq,))
     tau = np.zeros((nfreq, 2, 2))
-    _check(_lib.yf_read_sparams(C.c_void_p(g), z_ref, ssp, sp, zrp, zcp, tau.ctypes.data_as(_dp)))
+    if kind == DFT_FP64:
+        _check(_lib.yf_read_sparams(C.c_void_p(g), z_ref, ssp, sp, zrp, zcp, tau.ctypes.data_as(_dp)))
+    else:
+        _check(_lib.yf_read_sparams_acc(C.c_void_p(g), kind, z_ref, ssp, sp, zrp, zcp,
+                                        tau.ctypes.data_as(_dp)))
     return dict(S_star=_as_complex(ss), S=_as_complex(s), Zr=_as_complex(zr), Zc=_as_complex(zc),
                 tau=tau)
 
@@ -354,6 +360,12 @@ def profile_steps(g, n):
     nk = C.c_int()
     _check(_lib.yf_profile_steps(C.c_void_p(g), int(n), ms, C.byref(nk)))
     return {_lib.yf_kernel_name(C.c_void_p(g), q).decode(): ms[q] for q in range(nk.value)}
+
+
+def launches_per_step(g) -> int:
+    n = C.c_int()
+    _check(_lib.yf_launches_per_step(C.c_void_p(g), C.byref(n)))
+    return n.value
 
 
 def checkpoint_save(g, path):
@@ -441,6 +453,10 @@ class Grid:
         for q in range(self.nports):
             V[q], I[q] = read_port_dft(self.h, q, nf, kind)
         return V, I
+
+    def sparams(self, kind=DFT_FP64, z_ref=50.0):
+        """Uniform-line extraction (two ports, driven at port 0) from accumulator set `kind`."""
+        return read_sparams(self.h, len(self.prob.freqs), z_ref, kind)
 
     def close(self):
         if self.h is not None:
