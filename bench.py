@@ -30,9 +30,11 @@ UNIT = "Gcell-updates/s"
 BYTES_PER_CELL_FP32 = 51.0   # 6 components read + written once (48 B) + 3 edge-class bytes
 
 
-def workload():
+def workload(nz: int = 256):
+    """The lossy line; a smaller nz (same stack, fewer planes of air) is only for profiling
+    captures that must stay small."""
     from paper_2208_04371_b300 import workloads as W
-    return W.config_lossy_line(nsteps=0)
+    return W.config_lossy_line(nz=nz, nsteps=0)
 
 
 def peaks():
@@ -197,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    p = workload()
+    p = workload(args.nz)
     stream = torch.cuda.Stream()
     g = yf.Grid(p, prec=yf.FP32, stream=stream.cuda_stream)
     chunk = args.chunk
@@ -247,20 +249,23 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the public API: new geometry from pinned host memory every step
     # (yf_reset + yf_set_materials), the chunk of steps, and the port spectra read back
-    ids_host = torch.from_numpy(p.ids).pin_memory()
-    e2e_ms = []
-    nf = len(p.freqs)
-    for it in range(max(3, args.steps // 4) + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        yf.reset(g.h)
-        yf.set_materials(g.h, ids_host, p.eps_r, p.sigma, p.mu_r, p.is_pec)
-        g.step(chunk)
-        V, I = yf.read_port_dft(g.h, 0, nf)
-        V2, I2 = yf.read_port_dft(g.h, 1, nf)
-        if it > 0:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = p.cells * chunk * world / (np.median(e2e_ms) / 1e3) / 1e9
+    e2e = None
+    if not args.no_e2e:
+        ids_host = torch.from_numpy(p.ids).pin_memory()
+        e2e_ms = []
+        nf = len(p.freqs)
+        for it in range(max(3, args.steps // 4) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            yf.reset(g.h)
+            yf.set_materials(g.h, ids_host, p.eps_r, p.sigma, p.mu_r, p.is_pec)
+            g.step(chunk)
+            V, I = yf.read_port_dft(g.h, 0, nf)
+            V2, I2 = yf.read_port_dft(g.h, 1, nf)
+            if it > 0:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": p.cells * chunk * world / (np.median(e2e_ms) / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(p.ids.nbytes), "d2h_bytes_per_step": int(2 * 4 * nf * 8)}
     g.close()
 
     batched = None if args.no_batched else batched_leg(stream)
@@ -280,8 +285,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(p.ids.nbytes),
-                    "d2h_bytes_per_step": int(2 * 4 * nf * 8)},
+            "e2e": e2e,
             "gpu_launches": launches_per_step * chunk * args.steps,
             "clocks": clocks,
             "batched": batched,
@@ -298,6 +302,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nz", type=int, default=256,
+                    help="planes of the lossy line (profiling captures only; the bench line is nz=256)")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -264,6 +264,13 @@ const char *yf_kernel_name(yf_grid *g, int idx);
  * geometry like a first yf_step would. */
 yf_status yf_launches_per_step(yf_grid *g, int *n);
 
+/* Failure-detection check, no counterpart in the paper: one device thread waits, with the
+ * library's bounded-wait rule (a %globaltimer limit, never an unbounded spin), for a flag that
+ * is set beforehand when preset_flag != 0 and never set otherwise.  Returns YF_OK when the
+ * flag was seen and YF_E_TIMEOUT when the wait gave up after limit_seconds (0 < limit <= 10);
+ * either way the CUDA context stays usable.  Synchronous on the legacy default stream. */
+yf_status yf_bounded_wait_check(int preset_flag, double limit_seconds);
+
 /* Binary checkpoint of fields, CPML auxiliaries, DFT accumulators and the step count;
  * load requires a grid created and configured identically. */
 yf_status yf_checkpoint_save(yf_grid *g, const char *path);

@@ -30,6 +30,7 @@ yf_status fail(yf_status s, const char *fmt, ...)
 
 yf_status cuda_fail(cudaError_t e, const char *what)
 {
+    cudaGetLastError();   // clear a non-sticky error (e.g. a failed allocation) for later checks
     if (e == cudaErrorMemoryAllocation) return fail(YF_E_OOM, "%s: %s", what, cudaGetErrorString(e));
     return fail(YF_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -239,6 +239,42 @@ def config_long_run(nsteps: int = 1_000_000, ringing: bool = False, nfreq: int =
                       name="long-run 256x128x128" + (" ringing" if ringing else ""))
 
 
+SURROGATE_LO = (4.0, 0.0, 6.0, 2.0, 0.0, 32.0)
+SURROGATE_HI = (40.0, 10.0, 30.0, 12.0, 50.0, 160.0)
+
+
+def surrogate_line(desc, nsteps: int = 8000, nfreq: int = 128, pml: int = 8) -> Problem:
+    """The uniform microstrip a surrogate descriptor (width, thickness, substrate height in
+    cells, eps_r, substrate sigma [S/m], length in cells) stands for: 5 um cells, PEC ground,
+    strip of `thickness` PEC cells on the substrate (a zero-thickness sheet when 0), `length`
+    cells between the two ports, port 1 ten cells past the source, 8-cell PML elsewhere,
+    128 frequencies over 100-500 GHz."""
+    w, tk, h = int(round(desc[0])), int(round(desc[1])), int(round(desc[2]))
+    er, sg, L = float(desc[3]), float(desc[4]), int(round(desc[5]))
+    gap_y, air = max(6, h), max(8, h)
+    ny = w + 2 * gap_y + 2 * pml
+    nz = h + tk + air + pml
+    src = pml + 2
+    p1 = src + 10
+    p2 = p1 + L
+    nx = p2 + 6 + pml
+    j0 = pml + gap_y
+    prob = microstrip(nx, ny, nz, 5e-6, sub_cells=h, strip_j0=j0, strip_j1=j0 + w, eps_r=er,
+                      sigma=sg, pml=pml, bc=(BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML),
+                      courant=0.99, nsteps=nsteps, freqs=linear_freqs(100e9, 500e9, nfreq),
+                      f0=300e9, bw=200e9, src_plane=src, port_planes=(p1, p2),
+                      name=f"line w{w} t{tk} h{h} er{er:.2f} s{sg:.1f} L{L}")
+    if tk > 0:
+        ids = prob.ids.copy()
+        ids[h:h + tk, j0:j0 + w, :] = 2
+        prob = prob.replace(ids=ids, eps_r=np.append(prob.eps_r, 1.0),
+                            sigma=np.append(prob.sigma, 0.0), mu_r=np.append(prob.mu_r, 1.0),
+                            is_pec=np.append(prob.is_pec, 1).astype(np.uint8))
+        for pt in prob.ports:
+            pt.kt = h + tk
+    return prob
+
+
 def surrogate_inputs(rng: SplitMix64, n: int) -> np.ndarray:
     """Line descriptors for the surrogate: (width cells 4-40, thickness cells 0-10,
     substrate cells 6-30, eps_r 2-12, sigma S/m 0-50, length cells 32-160)."""
@@ -247,6 +283,38 @@ def surrogate_inputs(rng: SplitMix64, n: int) -> np.ndarray:
         out[r] = (rng.randint(4, 40), rng.randint(0, 10), rng.randint(6, 30),
                   rng.uniform(2.0, 12.0), rng.uniform(0.0, 50.0), rng.randint(32, 160))
     return out
+
+
+def splitmix64_array(seed: int, n: int) -> np.ndarray:
+    """The first n outputs of SplitMix64(seed), vectorised: output i mixes seed + (i+1) gamma."""
+    with np.errstate(over="ignore"):
+        st = np.uint64(seed & SplitMix64.MASK) + (np.arange(1, n + 1, dtype=np.uint64)
+                                                  * np.uint64(0x9E3779B97F4A7C15))
+        z = (st ^ (st >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_array(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    return lo + (hi - lo) * ((splitmix64_array(seed, n) >> np.uint64(11)).astype(np.float64)
+                             * (1.0 / (1 << 53)))
+
+
+MLP_SIZES = (6, 512, 512, 512, 512, 512)
+
+
+def mlp_init(seed: int, bias_scale: float = 0.0, sizes=MLP_SIZES) -> np.ndarray:
+    """Seeded initial surrogate weights, flat in the yfmlp.h layout (W_l [out][in], b_l):
+    uniform with variance 2 / fan_in for the GELU layers, 1 / fan_in for the linear output
+    layer; biases uniform in [-bias_scale, bias_scale]."""
+    parts = []
+    for l, (fin, fout) in enumerate(zip(sizes[:-1], sizes[1:])):
+        last = l == len(sizes) - 2
+        a = np.sqrt((3.0 if last else 6.0) / fin)
+        parts.append(uniform_array(seed * 1000003 + 2 * l, fin * fout, -a, a))
+        parts.append(uniform_array(seed * 1000003 + 2 * l + 1, fout, -bias_scale, bias_scale)
+                     if bias_scale > 0 else np.zeros(fout))
+    return np.concatenate(parts)
 
 
 def random_fields(shape_zyx: tuple, seed: int) -> np.ndarray:

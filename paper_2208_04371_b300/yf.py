@@ -101,6 +101,7 @@ _SIGS = {
     "yf_read_sparams": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_read_sparams_acc": (_i, [_vp, _i, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_launches_per_step": (_i, [_vp, C.POINTER(_i)]),
+    "yf_bounded_wait_check": (_i, [_i, _d]),
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
     "yf_set_variant": (_i, [_vp, _i, _i, _i]),
@@ -116,6 +117,16 @@ _SIGS = {
     "yf_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_long), _dp, C.POINTER(C.c_long)]),
     "yf_batch_grid": (_i, [_vp, _i, C.POINTER(_vp)]),
     "yf_batch_read_port_dft": (_i, [_vp, _i, _i, _i, _dp, _dp, _dp, _dp]),
+    "yf_mlp_create": (_i, [_i, _i, _i, _dp, _dp, _vp, C.POINTER(_vp)]),
+    "yf_mlp_destroy": (_i, [_vp]),
+    "yf_mlp_set_params": (_i, [_vp, _i, _dp]),
+    "yf_mlp_get_params": (_i, [_vp, _i, _dp]),
+    "yf_mlp_set_adam": (_i, [_vp, _d, _d, _d, _d]),
+    "yf_mlp_grads": (_i, [_vp, _i, _vp, _vp, _i, _dp, _dp]),
+    "yf_mlp_train_step": (_i, [_vp, _i, _vp, _vp, _i, _dp]),
+    "yf_mlp_query": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i]),
+    "yf_mlp_gate": (_i, [_vp, _vp, _i, _d, _d, _i, _vp, C.POINTER(_i)]),
+    "yf_mlp_query_stats": (_i, [_vp, C.POINTER(_i), _dp]),
     "yf_checkpoint_save": (_i, [_vp, C.c_char_p]),
     "yf_checkpoint_load": (_i, [_vp, C.c_char_p]),
 }
@@ -362,6 +373,10 @@ def profile_steps(g, n):
     return {_lib.yf_kernel_name(C.c_void_p(g), q).decode(): ms[q] for q in range(nk.value)}
 
 
+def bounded_wait_check(preset_flag: bool, limit_seconds: float):
+    _check(_lib.yf_bounded_wait_check(1 if preset_flag else 0, limit_seconds))
+
+
 def launches_per_step(g) -> int:
     n = C.c_int()
     _check(_lib.yf_launches_per_step(C.c_void_p(g), C.byref(n)))
@@ -585,6 +600,132 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             _lib.yf_batch_destroy(C.c_void_p(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- surrogate MLP (yfmlp.h)
+
+MLP_IN, MLP_WIDTH, MLP_OUT, MLP_LAYERS, MLP_PARAMS = 6, 512, 512, 5, 1054208
+
+
+def mlp_unflatten(flat: np.ndarray):
+    """Flat parameter vector -> [(W_l (out, in), b_l (out,))] in the yfmlp.h layout."""
+    out, off = [], 0
+    for l in range(MLP_LAYERS):
+        fin = MLP_IN if l == 0 else MLP_WIDTH
+        W = flat[off:off + MLP_WIDTH * fin].reshape(MLP_WIDTH, fin)
+        off += MLP_WIDTH * fin
+        b = flat[off:off + MLP_WIDTH]
+        off += MLP_WIDTH
+        out.append((W, b))
+    assert off == MLP_PARAMS
+    return out
+
+
+def mlp_flatten(params) -> np.ndarray:
+    return np.concatenate([np.concatenate([np.asarray(W).ravel(), np.asarray(b).ravel()])
+                           for W, b in params])
+
+
+class Mlp:
+    """Owns one yf_mlp handle (an ensemble of `members` surrogate networks)."""
+
+    def __init__(self, members: int, train_batch: int, max_query: int, in_lo, in_hi, stream=None):
+        h = C.c_void_p()
+        lo, klo = _f64(in_lo)
+        hi, khi = _f64(in_hi)
+        s = C.c_void_p(int(stream)) if stream else None
+        _check(_lib.yf_mlp_create(members, train_batch, max_query, lo, hi, s, C.byref(h)))
+        self.h = h.value
+        self.members, self.batch, self.max_query = members, train_batch, max_query
+
+    def set_params(self, member: int, flat: np.ndarray):
+        p, k = _f64(flat)
+        assert k.size == MLP_PARAMS
+        _check(_lib.yf_mlp_set_params(C.c_void_p(self.h), member, p))
+
+    def get_params(self, member: int) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS)
+        _check(_lib.yf_mlp_get_params(C.c_void_p(self.h), member, out.ctypes.data_as(_dp)))
+        return out
+
+    def set_adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(_lib.yf_mlp_set_adam(C.c_void_p(self.h), lr, beta1, beta2, eps))
+
+    @staticmethod
+    def _f32(a):
+        if hasattr(a, "data_ptr"):
+            assert str(a.dtype) == "torch.float32"
+            a = a.contiguous()
+            return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST), a
+        arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+        return C.c_void_p(arr.ctypes.data), HOST, arr
+
+    def grads(self, member: int, x, t):
+        """(loss, flat gradient) of one batch, no update."""
+        px, wx, kx = self._f32(x)
+        pt, wt, kt = self._f32(t)
+        assert wx == wt
+        loss = C.c_double()
+        g = np.zeros(MLP_PARAMS)
+        _check(_lib.yf_mlp_grads(C.c_void_p(self.h), member, px, pt, wx, C.byref(loss),
+                                 g.ctypes.data_as(_dp)))
+        return loss.value, g
+
+    def train_step(self, member: int, x, t, want_loss: bool = False):
+        px, wx, kx = self._f32(x)
+        pt, wt, kt = self._f32(t)
+        assert wx == wt
+        loss = C.c_double()
+        _check(_lib.yf_mlp_train_step(C.c_void_p(self.h), member, px, pt, wx,
+                                      C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def query(self, x, y=None, est=None):
+        """Ensemble mean [n, 512] and disagreement [n].  With torch CUDA tensors y and est given,
+        everything stays on the device (asynchronous)."""
+        px, wx, kx = self._f32(x)
+        n = int(kx.shape[0])
+        if y is None:
+            yo = np.zeros((n, MLP_OUT), dtype=np.float32)
+            eo = np.zeros(n, dtype=np.float32)
+            _check(_lib.yf_mlp_query(C.c_void_p(self.h), px, n, wx, C.c_void_p(yo.ctypes.data),
+                                     C.c_void_p(eo.ctypes.data), HOST))
+            return yo, eo
+        _check(_lib.yf_mlp_query(C.c_void_p(self.h), px, n, wx, C.c_void_p(y.data_ptr()),
+                                 C.c_void_p(est.data_ptr()) if est is not None else None, DEVICE))
+        return y, est
+
+    def gate(self, est, scale: float, threshold: float):
+        """(flags int32 [n], number flagged) for host est."""
+        e = np.ascontiguousarray(np.asarray(est, dtype=np.float32))
+        flags = np.zeros(e.size, dtype=np.int32)
+        cnt = C.c_int()
+        _check(_lib.yf_mlp_gate(C.c_void_p(self.h), C.c_void_p(e.ctypes.data), e.size, scale,
+                                threshold, HOST, C.c_void_p(flags.ctypes.data), C.byref(cnt)))
+        return flags, cnt.value
+
+    def query_stats(self):
+        n = C.c_int()
+        fl = C.c_double()
+        _check(_lib.yf_mlp_query_stats(C.c_void_p(self.h), C.byref(n), C.byref(fl)))
+        return n.value, fl.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.yf_mlp_destroy(C.c_void_p(self.h))
             self.h = None
 
     def __enter__(self):

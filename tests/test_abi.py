@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(yf):
     missing = [n for n in declared if not hasattr(lib, n)]
     assert not missing, missing
     # the binding wraps every declared entry point with its own signature
-    assert declared <= set(yf.DECLARED) | {n for n in declared if n.startswith("yf_batch") or n.startswith("yf_mlp")}
+    assert declared <= set(yf.DECLARED)
 
 
 def test_courant_dt_host_only(yf):
