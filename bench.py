@@ -186,6 +186,46 @@ def batched_leg(stream, steps: int = 64) -> dict:
             "accuracy": "FP32 fields, FP64 spectra: <= 1e-3 in |S_ij| vs the FP64 run"}
 
 
+def surrogate_leg(stream, n: int = 65536, members: int = 4, reps: int = 20) -> dict:
+    """Surrogate ensemble inference: `members` networks (6 -> 4 x 512 GELU -> 512, BF16
+    tcgen05 GEMMs, FP32 accumulation) on a batch of n seeded line descriptors, ensemble mean,
+    disagreement and gate.  Timed with CUDA events on the library's stream; inputs resident."""
+    import torch
+    from paper_2208_04371_b300 import workloads as W
+    from paper_2208_04371_b300 import yf
+    m = yf.Mlp(members, 512, n, W.SURROGATE_LO, W.SURROGATE_HI, stream=stream.cuda_stream)
+    try:
+        for e in range(members):
+            m.set_params(e, W.mlp_init(0x5EED + 7919 * e))
+        xh = np.stack([W.uniform_array(0x51 + k, n, lo, hi) for k, (lo, hi) in
+                       enumerate(zip(W.SURROGATE_LO, W.SURROGATE_HI))], axis=1).astype(np.float32)
+        x = torch.from_numpy(xh).cuda()
+        y = torch.empty((n, yf.MLP_OUT), dtype=torch.float32, device="cuda")
+        est = torch.empty(n, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(3):
+            m.query(x, y, est)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            m.query(x, y, est)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        launches, flops_per_query = m.query_stats()
+    finally:
+        m.close()
+    tflops = flops_per_query * n / (ms / 1e3) / 1e12
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1800.0}
+    return {"workload": f"{members}-member ensemble, {n} queries per batch",
+            "queries_per_s": n / (ms / 1e3), "ms_per_batch": ms, "launches_per_batch": launches,
+            "gemm_tflops": tflops, "bf16_peak_tflops": pk["bf16_tflops"],
+            "frac_of_bf16_peak": tflops / pk["bf16_tflops"]}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2208_04371_b300 import yf
@@ -269,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
     g.close()
 
     batched = None if args.no_batched else batched_leg(stream)
+    sur = None if args.no_surrogate else surrogate_leg(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -289,6 +330,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches_per_step * chunk * args.steps,
             "clocks": clocks,
             "batched": batched,
+            "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
 
@@ -303,6 +345,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="only the surrogate inference leg (profiling captures)")
     ap.add_argument("--nz", type=int, default=256,
                     help="planes of the lossy line (profiling captures only; the bench line is nz=256)")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
@@ -312,6 +357,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.surrogate_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"surrogate": surrogate_leg(torch.cuda.Stream())}), flush=True)
         return
     if world > 1:
         import torch

@@ -73,6 +73,23 @@ yf_status yf_mlp_grads(yf_mlp *m, int member, const float *x, const float *t, yf
 yf_status yf_mlp_train_step(yf_mlp *m, int member, const float *x, const float *t,
                             yf_mem where, double *loss);
 
+/* Many Adam steps of one member from device-resident data, replayed from one captured CUDA
+ * graph of the whole step (batch gather, forward, loss, backward, Adam, BF16 publish):
+ *   x [n][6], t [n][512] float32 DEVICE arrays (the training set);
+ *   idx [steps * train_batch] int32 DEVICE: rows of step s are idx[s*B .. s*B + B - 1], each in
+ *     [0, n) (an out-of-range row stops that step's gather and makes yf_mlp_sync report
+ *     YF_E_INVALID);
+ *   lr [steps] float32 DEVICE: the learning rate of each step.
+ * Asynchronous; the arrays must stay valid until the work completes (yf_mlp_sync).  The graph
+ * is kept and reused while the same pointers and n are passed again. */
+yf_status yf_mlp_fit(yf_mlp *m, int member, const float *x, const float *t, int n,
+                     const int32_t *idx, const float *lr, long steps);
+
+/* Wait for the handle's queued work; report a device-side failure (YF_E_TIMEOUT for a wait
+ * that gave up, YF_E_INVALID for an out-of-range training row); *loss (nullable) = the loss
+ * of the last training batch. */
+yf_status yf_mlp_sync(yf_mlp *m, double *loss);
+
 /* Ensemble inference: x [n][6] raw descriptors (1 <= n <= max_query, `where`).
  * y [n][512] receives the ensemble mean; est [n] (nullable) the disagreement
  * max over members, S entries (S11, S21) and frequencies of |S_member - S_mean| (complex

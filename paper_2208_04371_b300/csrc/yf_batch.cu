@@ -2,9 +2,9 @@
 //
 // Each instance is an ordinary yf_grid configured through the single-grid set-up calls
 // (materials, sheets, boundaries, CPML, source, ports), so every instance computes exactly
-// what the single-grid path computes.  A batch step is three launches for all instances
-// together: the CPML-free interior work items, the CPML frame work items (side stream), and
-// a one-block-per-instance port epilogue.  A work item is one 32 x tile_y node column of one
+// what the single-grid path computes.  A batch step is at most six launches for all instances
+// together: the CPML-free interior work items, up to four kinds of CPML frame work items (x,
+// y, z, or all slabs; on a side stream), and a one-block-per-instance port epilogue.  A work item is one 32 x tile_y node column of one
 // instance over a z-segment; per-instance kernel arguments and tensor maps live in device
 // memory, two sets each (field-buffer parity 0 and 1).  Chunks of steps replay from
 // captured CUDA graphs.

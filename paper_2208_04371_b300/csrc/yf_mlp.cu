@@ -37,7 +37,6 @@ constexpr int kIn = YF_MLP_IN, kWidth = YF_MLP_WIDTH, kOut = YF_MLP_OUT, kLayers
 constexpr int kK1 = 64;        // layer-1 K padded to one 64-wide slice (6 real columns)
 constexpr int kBM = 128;       // rows per tile (tcgen05 M)
 constexpr int kBK = 64;        // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kStages = 4;
 constexpr int kThreads = 192;  // producer warp, MMA warp, four epilogue warps
 constexpr long kParams = YF_MLP_PARAMS;
 
@@ -218,7 +217,7 @@ struct GemmArgs {
     int *status;
 };
 
-template <int NT>
+template <int NT, int kStages>
 struct GemmSmem {
     static constexpr int A_BYTES = kBM * kBK * 2;            // 16 KB
     static constexpr int B_BYTES = NT * kBK * 2;
@@ -228,11 +227,11 @@ struct GemmSmem {
     static constexpr uint32_t TMEM_COLS = NT < 32 ? 32 : NT;
 };
 
-template <int NT>
+template <int NT, int kStages>
 __global__ void __launch_bounds__(kThreads, 1)
 k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g)
 {
-    using S = GemmSmem<NT>;
+    using S = GemmSmem<NT, kStages>;
     extern __shared__ uint8_t smem_raw[];
     // stage bases 1024-byte aligned in the shared window (the 128-byte swizzle repeats every
     // 8 rows of 128 bytes and is computed from the address bits)
@@ -467,18 +466,53 @@ __global__ void k_rowsum(const bf16 *dzt, int B, int N, float *db)
     if (lane == 0) db[n] = s;
 }
 
-// Adam with bias correction (c1 = 1 - b1^k, c2 = 1 - b2^k) on the flat FP32 parameters
-__global__ void k_adam(float *p, float *m, float *v, const float *g, long n, float lr, float b1,
-                       float b2, float eps, float c1, float c2)
+// Adam with bias correction on the flat FP32 parameters.  The step number k = *kstep + 1 and
+// the learning rate (lr_sched[*pos] when a schedule is given, else lr) come from device
+// memory, so a captured step replays correctly; k_advance moves both counters afterwards.
+struct AdamArgs {
+    float *p, *m, *v;
+    const float *g;
+    long n;
+    float lr, b1, b2, eps;
+    const long long *kstep;
+    const float *lr_sched;
+    const int *pos;
+};
+
+__global__ void k_adam(AdamArgs a)
 {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const double k = (double)(*a.kstep + 1);
+    const float c1 = (float)(1.0 - pow((double)a.b1, k));
+    const float c2 = (float)(1.0 - pow((double)a.b2, k));
+    const float lr = a.lr_sched ? a.lr_sched[*a.pos] : a.lr;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = a.g[i];
+        const float mi = a.b1 * a.m[i] + (1.f - a.b1) * gi;
+        const float vi = a.b2 * a.v[i] + (1.f - a.b2) * gi * gi;
+        a.m[i] = mi;
+        a.v[i] = vi;
+        a.p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + a.eps);
     }
+}
+
+__global__ void k_advance(long long *kstep, int *pos)
+{
+    *kstep += 1;
+    if (pos) *pos += 1;
+}
+
+// training batch of step *pos: rows idx[*pos * B + r] of x [n][6] and t [n][512]
+__global__ void k_gather(const float *x, const float *t, const int32_t *idx, const int *pos, int B,
+                         int n, float *xin, float *tin, int *status)
+{
+    const int r = blockIdx.x;
+    const long row = idx[(long)(*pos) * B + r];
+    if (row < 0 || row >= n) {
+        if (threadIdx.x == 0) atomicOr(status, 4);
+        return;
+    }
+    for (int c = threadIdx.x; c < kOut; c += blockDim.x) tin[(long)r * kOut + c] = t[row * kOut + c];
+    if (threadIdx.x < kIn) xin[(long)r * kIn + threadIdx.x] = x[row * kIn + threadIdx.x];
 }
 
 // FP32 master weights -> BF16 stack [5 * 512][512] (layer l at rows l * 512, K-padded) and the
@@ -551,7 +585,12 @@ struct yf_mlp {
     bool own_stream = false;
     InMap in;
     double lr = 1e-3, b1 = 0.9, b2 = 0.999, eps = 1e-8;
-    std::vector<long> steps;
+    long long *kstep = nullptr;   // per member Adam step count (device)
+    int *pos = nullptr;           // step index inside the current yf_mlp_fit call (device)
+    // captured training step per member, valid for the pointers it was captured with
+    std::vector<cudaGraphExec_t> fit_graph;
+    struct FitKey { const void *x, *t, *idx, *lr; int n; };
+    std::vector<FitKey> fit_key;
     // per member
     std::vector<float *> master, mom, vel, grad;
     std::vector<bf16 *> wst, wtst;
@@ -617,25 +656,32 @@ yf_status dalloc(yf_mlp *m, T **p, size_t count)
     return YF_OK;
 }
 
-template <int NT>
+template <int NT, int ST>
 cudaError_t prepare_gemm()
 {
-    return cudaFuncSetAttribute(k_mlp_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GemmSmem<NT>::BYTES);
+    return cudaFuncSetAttribute(k_mlp_gemm<NT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                GemmSmem<NT, ST>::BYTES);
 }
 
-template <int NT>
+template <int NT, int ST>
 cudaError_t launch_gemm_t(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s)
 {
     dim3 grid(g.P / kBM, g.Q / NT);
-    k_mlp_gemm<NT><<<grid, kThreads, GemmSmem<NT>::BYTES, s>>>(a, b, g);
+    k_mlp_gemm<NT, ST><<<grid, kThreads, GemmSmem<NT, ST>::BYTES, s>>>(a, b, g);
     return cudaGetLastError();
 }
 
+// Large grids (at least two tiles per SM) take 2 stages: 96 KB of shared memory and 256 TMEM
+// columns per CTA let two CTAs share an SM, so one's epilogue overlaps the other's MMAs.
+// Small grids (the training GEMMs) keep 4 stages for a deeper copy pipeline.
 cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s)
 {
-    if (g.Q % 256 == 0) return launch_gemm_t<256>(a, b, g, s);
-    return launch_gemm_t<64>(a, b, g, s);
+    if (g.Q % 256 == 0) {
+        const long tiles = (long)(g.P / kBM) * (g.Q / 256);
+        if (tiles >= 2 * 148) return launch_gemm_t<256, 2>(a, b, g, s);
+        return launch_gemm_t<256, 4>(a, b, g, s);
+    }
+    return launch_gemm_t<64, 4>(a, b, g, s);
 }
 
 GemmArgs args(yf_mlp *m, int P, int Q, int R, int mode)
@@ -653,7 +699,8 @@ yf_status check_status(yf_mlp *m)
     YF_CUDA_TRY(cudaStreamSynchronize(m->stream));
     if (st) {
         YF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), m->stream));
-        return fail(YF_E_TIMEOUT, "yf_mlp: a tensor-core pipeline wait gave up (status %d)", st);
+        if (st & 2) return fail(YF_E_TIMEOUT, "yf_mlp: a tensor-core pipeline wait gave up (status %d)", st);
+        return fail(YF_E_INVALID, "yf_mlp_fit: a training row index was outside [0, n)");
     }
     return YF_OK;
 }
@@ -721,6 +768,22 @@ yf_status publish(yf_mlp *m, int mem)
     return YF_OK;
 }
 
+cudaError_t adam_step(yf_mlp *m, int mem, const float *lr_sched)
+{
+    AdamArgs a;
+    a.p = m->master[mem]; a.m = m->mom[mem]; a.v = m->vel[mem]; a.g = m->grad[mem];
+    a.n = kParams;
+    a.lr = (float)m->lr; a.b1 = (float)m->b1; a.b2 = (float)m->b2; a.eps = (float)m->eps;
+    a.kstep = m->kstep + mem;
+    a.lr_sched = lr_sched;
+    a.pos = m->pos;
+    k_adam<<<148 * 8, 256, 0, m->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_advance<<<1, 1, 0, m->stream>>>(m->kstep + mem, lr_sched ? m->pos : nullptr);
+    return cudaGetLastError();
+}
+
 bool bad_member(yf_mlp *m, int mem) { return !m || mem < 0 || mem >= m->E; }
 
 }  // namespace
@@ -758,7 +821,8 @@ yf_status yf_mlp_create(int members, int train_batch, int max_query, const doubl
             return bail(cuda_fail(cudaGetLastError(), "cudaStreamCreateWithFlags"));
         m->own_stream = true;
     }
-    if (prepare_gemm<256>() != cudaSuccess || prepare_gemm<64>() != cudaSuccess)
+    if (prepare_gemm<256, 2>() != cudaSuccess || prepare_gemm<256, 4>() != cudaSuccess ||
+        prepare_gemm<64, 4>() != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaFuncSetAttribute(k_mlp_gemm)"));
     yf_status st;
 #define TRY(x)                                \
@@ -766,7 +830,8 @@ yf_status yf_mlp_create(int members, int train_batch, int max_query, const doubl
         if ((st = (x)) != YF_OK) return bail(st); \
     } while (0)
     const long stackn = (long)kLayers * kWidth * kWidth;
-    m->steps.assign(members, 0);
+    m->fit_graph.assign(members, nullptr);
+    m->fit_key.assign(members, yf_mlp::FitKey{nullptr, nullptr, nullptr, nullptr, 0});
     m->master.resize(members); m->mom.resize(members); m->vel.resize(members); m->grad.resize(members);
     m->wst.resize(members); m->wtst.resize(members); m->mW.resize(members); m->mWT.resize(members);
     for (int e = 0; e < members; ++e) {
@@ -815,6 +880,8 @@ yf_status yf_mlp_create(int members, int train_batch, int max_query, const doubl
     TRY(dalloc(m, &m->qest, (size_t)NQ));
     TRY(dalloc(m, &m->status, 1));
     TRY(dalloc(m, &m->count, 1));
+    TRY(dalloc(m, &m->kstep, (size_t)members));
+    TRY(dalloc(m, &m->pos, 1));
 #undef TRY
     *out = m;
     return YF_OK;
@@ -824,6 +891,8 @@ yf_status yf_mlp_destroy(yf_mlp *m)
 {
     if (!m) return YF_OK;
     if (m->stream) cudaStreamSynchronize(m->stream);
+    for (cudaGraphExec_t g : m->fit_graph)
+        if (g) cudaGraphExecDestroy(g);
     for (void *p : m->allocs) cudaFree(p);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -838,7 +907,7 @@ yf_status yf_mlp_set_params(yf_mlp *m, int member, const double *params)
     YF_CUDA_TRY(cudaMemcpyAsync(m->master[member], f.data(), kParams * sizeof(float), cudaMemcpyHostToDevice, m->stream));
     YF_CUDA_TRY(cudaMemsetAsync(m->mom[member], 0, kParams * sizeof(float), m->stream));
     YF_CUDA_TRY(cudaMemsetAsync(m->vel[member], 0, kParams * sizeof(float), m->stream));
-    m->steps[member] = 0;
+    YF_CUDA_TRY(cudaMemsetAsync(m->kstep + member, 0, sizeof(long long), m->stream));
     yf_status st = publish(m, member);
     if (st != YF_OK) return st;
     YF_CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -887,17 +956,61 @@ yf_status yf_mlp_train_step(yf_mlp *m, int member, const float *x, const float *
     yf_status st = stage_batch(m, x, t, where);
     if (st != YF_OK) return st;
     if ((st = train_pass(m, member)) != YF_OK) return st;
-    const long k = ++m->steps[member];
-    const double c1 = 1.0 - std::pow(m->b1, (double)k), c2 = 1.0 - std::pow(m->b2, (double)k);
-    k_adam<<<148 * 8, 256, 0, m->stream>>>(m->master[member], m->mom[member], m->vel[member], m->grad[member],
-                                          kParams, (float)m->lr, (float)m->b1, (float)m->b2, (float)m->eps,
-                                          (float)c1, (float)c2);
-    YF_CUDA_TRY(cudaGetLastError());
+    YF_CUDA_TRY(adam_step(m, member, nullptr));
     if ((st = publish(m, member)) != YF_OK) return st;
     if (loss) {
         if ((st = check_status(m)) != YF_OK) return st;
         YF_CUDA_TRY(cudaMemcpy(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
     }
+    return YF_OK;
+}
+
+yf_status yf_mlp_fit(yf_mlp *m, int member, const float *x, const float *t, int n,
+                     const int32_t *idx, const float *lr, long steps)
+{
+    if (bad_member(m, member) || !x || !t || !idx || !lr || n < 1 || steps < 0)
+        return fail(YF_E_INVALID, "yf_mlp_fit: bad argument");
+    if (steps == 0) return YF_OK;
+    yf_mlp::FitKey key{x, t, idx, lr, n};
+    yf_mlp::FitKey &old = m->fit_key[member];
+    const bool same = old.x == key.x && old.t == key.t && old.idx == key.idx && old.lr == key.lr &&
+                      old.n == key.n;
+    if (!m->fit_graph[member] || !same) {
+        if (m->fit_graph[member]) {
+            cudaGraphExecDestroy(m->fit_graph[member]);
+            m->fit_graph[member] = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        YF_CUDA_TRY(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+        k_gather<<<m->B, 128, 0, m->stream>>>(x, t, idx, m->pos, m->B, n, m->xin, m->tin, m->status);
+        yf_status st = train_pass(m, member);
+        cudaError_t e = st == YF_OK ? adam_step(m, member, lr) : cudaSuccess;
+        if (e == cudaSuccess && st == YF_OK) st = publish(m, member);
+        cudaError_t ec = cudaStreamEndCapture(m->stream, &graph);
+        if (st != YF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e != cudaSuccess ? e : ec, "capturing the training step");
+        }
+        e = cudaGraphInstantiate(&m->fit_graph[member], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(training step)");
+        old = key;
+    }
+    YF_CUDA_TRY(cudaMemsetAsync(m->pos, 0, sizeof(int), m->stream));
+    for (long s = 0; s < steps; ++s) YF_CUDA_TRY(cudaGraphLaunch(m->fit_graph[member], m->stream));
+    return YF_OK;
+}
+
+yf_status yf_mlp_sync(yf_mlp *m, double *loss)
+{
+    if (!m) return fail(YF_E_INVALID, "yf_mlp_sync: NULL handle");
+    yf_status st = check_status(m);
+    if (st != YF_OK) return st;
+    if (loss) YF_CUDA_TRY(cudaMemcpy(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
     return YF_OK;
 }
 

@@ -81,27 +81,26 @@ class Surrogate:
 
     def fit(self, x: np.ndarray, t: np.ndarray, epochs: int, lr: float = 1e-3,
             lr_end: float = 2e-5, log=None) -> list:
-        """Adam on every member, each with its own seeded shuffles; learning rate decays
-        geometrically from lr to lr_end over the epochs.  Returns the last loss per member."""
+        """Adam on every member, each with its own seeded shuffle per epoch; the learning rate
+        decays geometrically from lr to lr_end.  One graph-replayed yf_mlp_fit call per member.
+        Returns the last batch loss per member."""
         import torch
         xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
         td = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).cuda()
         n = len(x)
-        steps = n // self.batch
+        per = n // self.batch
+        steps = per * epochs
+        sched = torch.from_numpy((lr * (lr_end / lr) ** (np.arange(steps) / max(steps - 1, 1)))
+                                 .astype(np.float32)).cuda()
         losses = []
         for e in range(self.members):
-            for ep in range(epochs):
-                frac = ep / max(epochs - 1, 1)
-                self.mlp.set_adam(lr=lr * (lr_end / lr) ** frac)
-                idx = torch.from_numpy(_perm(self.seed * 31 + e * 1000003 + ep, n)).cuda()
-                for s in range(steps):
-                    sel = idx[s * self.batch:(s + 1) * self.batch]
-                    self.mlp.train_step(e, xd[sel].contiguous(), td[sel].contiguous())
-            sel = idx[:self.batch]
-            losses.append(self.mlp.train_step(e, xd[sel].contiguous(), td[sel].contiguous(),
-                                               want_loss=True))
+            idx = np.concatenate([_perm(self.seed * 31 + e * 1000003 + ep, n)[:per * self.batch]
+                                  for ep in range(epochs)]).astype(np.int32)
+            idx_d = torch.from_numpy(idx).cuda()
+            self.mlp.fit(e, xd, td, idx_d, sched, steps)
+            losses.append(self.mlp.sync())
             if log:
-                log(f"member {e}: loss {losses[-1]:.3e}")
+                log(f"member {e}: {steps} steps, last batch loss {losses[-1]:.3e}")
         return losses
 
     def predict(self, x: np.ndarray):

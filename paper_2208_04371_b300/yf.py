@@ -127,6 +127,8 @@ _SIGS = {
     "yf_mlp_query": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i]),
     "yf_mlp_gate": (_i, [_vp, _vp, _i, _d, _d, _i, _vp, C.POINTER(_i)]),
     "yf_mlp_query_stats": (_i, [_vp, C.POINTER(_i), _dp]),
+    "yf_mlp_fit": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp, C.c_long]),
+    "yf_mlp_sync": (_i, [_vp, _dp]),
     "yf_checkpoint_save": (_i, [_vp, C.c_char_p]),
     "yf_checkpoint_load": (_i, [_vp, C.c_char_p]),
 }
@@ -692,6 +694,21 @@ class Mlp:
         _check(_lib.yf_mlp_train_step(C.c_void_p(self.h), member, px, pt, wx,
                                       C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def fit(self, member: int, x, t, idx, lr, steps: int):
+        """Graph-replayed Adam steps on device tensors: x [n, 6], t [n, 512] float32,
+        idx [steps * batch] int32 rows, lr [steps] float32.  Asynchronous (see sync)."""
+        for a in (x, t, idx, lr):
+            assert hasattr(a, "data_ptr") and a.is_cuda and a.is_contiguous()
+        assert idx.numel() >= steps * self.batch and lr.numel() >= steps
+        _check(_lib.yf_mlp_fit(C.c_void_p(self.h), member, C.c_void_p(x.data_ptr()),
+                               C.c_void_p(t.data_ptr()), int(x.shape[0]),
+                               C.c_void_p(idx.data_ptr()), C.c_void_p(lr.data_ptr()), int(steps)))
+
+    def sync(self) -> float:
+        loss = C.c_double()
+        _check(_lib.yf_mlp_sync(C.c_void_p(self.h), C.byref(loss)))
+        return loss.value
 
     def query(self, x, y=None, est=None):
         """Ensemble mean [n, 512] and disagreement [n].  With torch CUDA tensors y and est given,

@@ -136,3 +136,33 @@ def test_training_lowers_the_loss(gpu):
             m.train_step(0, x, t)
         last = m.train_step(0, x, t, want_loss=True)
     assert last < 0.05 * first, (first, last)
+
+
+def test_graph_replayed_fit_equals_step_by_step_training(gpu):
+    B, n, steps = 128, 384, 5
+    x = raw_inputs(10, n)
+    t = W.uniform_array(79, n * 512, -1.0, 1.0).reshape(n, 512).astype(np.float32)
+    idx = np.concatenate([np.argsort(W.splitmix64_array(100 + s, n))[:B] for s in range(steps)])
+    idx = idx.astype(np.int32)
+    lr = np.full(steps, 2e-3, dtype=np.float32)
+    flat = W.mlp_init(14, bias_scale=0.1)
+    with gpu.Mlp(1, B, 128, LO, HI) as m:
+        m.set_params(0, flat)
+        m.set_adam(lr=2e-3)
+        for s in range(steps):
+            rows = idx[s * B:(s + 1) * B]
+            m.train_step(0, x[rows], t[rows])
+        step_by_step = m.get_params(0)
+    with gpu.Mlp(1, B, 128, LO, HI) as m:
+        m.set_params(0, flat)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        m.fit(0, xd, td, torch.from_numpy(idx).cuda(), torch.from_numpy(lr).cuda(), steps)
+        m.sync()
+        replayed = m.get_params(0)
+        # an index outside the training set is reported, not read
+        bad = torch.from_numpy(np.full(B, n, dtype=np.int32)).cuda()
+        m.fit(0, xd, td, bad, torch.from_numpy(lr[:1]).cuda(), 1)
+        with pytest.raises(gpu.YFError) as e:
+            m.sync()
+        assert e.value.code == gpu.E_INVALID
+    assert np.array_equal(step_by_step, replayed)

@@ -1,6 +1,6 @@
 """Precision variants on the long-run workload (256x128x128 lossless eps_r 3.9 microstrip,
 256 frequencies): FP32 fields with FP64, Kahan-compensated FP32 and plain FP32 running-DFT
-accumulators (Sec. 2), the FP64-field GPU run as the long-run reference, and a 2000-step
+accumulators (the transforms of Sec. II-A, Eq. 1-2), the FP64-field GPU run as the long-run reference, and a 2000-step
 subrun against the FP64 oracle.
 
 Tolerances:
