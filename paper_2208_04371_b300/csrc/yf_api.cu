@@ -369,11 +369,7 @@ yf_status finalize(yf_grid *g)
         st = ensure_plan(g);
         if (st != YF_OK) return st;
     }
-    if (g->variant == 2 && !g->side.stream) {
-        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
-    }
+    if (g->variant == 2) YF_CUDA_TRY(side_create(&g->side));
     g->started = true;
     return YF_OK;
 }
@@ -530,12 +526,7 @@ yf_status yf_grid_destroy(yf_grid *g)
     }
     cudaFree(g->segs_dev); cudaFree(g->slots); cudaFree(g->ticket);
     free_plan(&g->plan);
-    if (g->side.stream) {
-        cudaStreamSynchronize(g->side.stream);
-        cudaEventDestroy(g->side.fork);
-        cudaEventDestroy(g->side.join);
-        cudaStreamDestroy(g->side.stream);
-    }
+    side_destroy(&g->side);
     cudaFree(g->ctab); cudaFree(g->eps_tab); cudaFree(g->ctr); cudaFree(g->status);
     cudaFree(g->energy_partials); cudaFree(g->ports_dev); cudaFree(g->inc_dev);
     cudaFree(g->acc64); cudaFree(g->acc32); cudaFree(g->kahan); cudaFree(g->src_table_dev);
@@ -990,11 +981,7 @@ yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
         yf_status st = ensure_plan(g);
         if (st != YF_OK) return st;
     }
-    if (g->started && variant == 2 && !g->side.stream) {
-        YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->side.stream, cudaStreamNonBlocking));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.fork, cudaEventDisableTiming));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&g->side.join, cudaEventDisableTiming));
-    }
+    if (g->started && variant == 2) YF_CUDA_TRY(side_create(&g->side));
     return YF_OK;
 }
 

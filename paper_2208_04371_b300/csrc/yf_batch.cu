@@ -2,12 +2,12 @@
 //
 // Each instance is an ordinary yf_grid configured through the single-grid set-up calls
 // (materials, sheets, boundaries, CPML, source, ports), so every instance computes exactly
-// what the single-grid path computes.  A batch step is at most six launches for all instances
-// together: the CPML-free interior work items, up to four kinds of CPML frame work items (x,
-// y, z, or all slabs; on a side stream), and a one-block-per-instance port epilogue.  A work item is one 32 x tile_y node column of one
-// instance over a z-segment; per-instance kernel arguments and tensor maps live in device
-// memory, two sets each (field-buffer parity 0 and 1).  Chunks of steps replay from
-// captured CUDA graphs.
+// what the single-grid path computes.  A batch step is at most six launches for all
+// instances together: the CPML-free interior work items, up to four kinds of CPML frame work
+// items (x, y, z, or all slabs; each on its own side stream), and a one-block-per-instance
+// port epilogue.  A work item is one 32 x tile_y node column of one instance over a
+// z-segment; per-instance kernel arguments and tensor maps live in device memory, two sets
+// each (field-buffer parity 0 and 1).  Chunks of steps replay from captured CUDA graphs.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -131,11 +131,7 @@ yf_status prepare(yf_batch *b)
     }
     yf_status st = b->prec == YF_FP32 ? build_tables<float>(b) : build_tables<double>(b);
     if (st != YF_OK) return st;
-    if (!b->side.stream) {
-        YF_CUDA_TRY(cudaStreamCreateWithFlags(&b->side.stream, cudaStreamNonBlocking));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&b->side.fork, cudaEventDisableTiming));
-        YF_CUDA_TRY(cudaEventCreateWithFlags(&b->side.join, cudaEventDisableTiming));
-    }
+    YF_CUDA_TRY(side_create(&b->side));
     b->started = true;
     return YF_OK;
 }
@@ -250,12 +246,7 @@ yf_status yf_batch_destroy(yf_batch *b)
     free_device(b);
     for (yf_grid *g : b->g) yf_grid_destroy(g);
     cudaFree(b->status);
-    if (b->side.stream) {
-        cudaStreamSynchronize(b->side.stream);
-        cudaEventDestroy(b->side.fork);
-        cudaEventDestroy(b->side.join);
-        cudaStreamDestroy(b->side.stream);
-    }
+    side_destroy(&b->side);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return YF_OK;

@@ -151,11 +151,17 @@ cudaError_t launch_fused(const FusedArgs<T> &a, int tile_y, cudaStream_t s);
 template <typename T>
 int tma_box_x(int tile_x);
 cudaError_t tma_prepare();
-// second stream of a grid for work that may overlap the main stream within a step
+// streams of a grid for work that may overlap the main stream within a step: one per CPML
+// work kind, forked from and joined back into the main stream (graph capture turns them into
+// parallel branches)
+constexpr int kSideStreams = 4;
 struct SideStream {
-    cudaStream_t stream;
-    cudaEvent_t fork, join;
+    cudaStream_t stream[kSideStreams];
+    cudaEvent_t fork, join[kSideStreams];
+    bool ready;
 };
+cudaError_t side_create(SideStream *s);
+void side_destroy(SideStream *s);
 // one block of the TMA-staged step: instance, tile origin (node indices), planes kb..ke
 struct BatchItem {
     int inst, i0, j0, kb, ke;

@@ -12,9 +12,9 @@
 // k_mlp_gemm: one 128 x NT output tile per CTA.  Warp 0 (one lane) streams 64-wide K slices
 // of A and B into a ring of shared-memory stages with TMA (128-byte swizzle); warp 1 owns the
 // tensor-memory allocation and (one lane) issues tcgen05.mma (M = 128, N = NT, K = 16) on the
-// staged slices, releasing each stage with tcgen05.commit; warps 2..5 wait for the final
-// commit, read the FP32 accumulator with tcgen05.ld (each warp its 32-lane quarter) and run
-// the epilogue.  Every mbarrier wait is bounded (2 s of %globaltimer); a wait that gives up
+// staged slices, releasing each stage with tcgen05.commit; warps 2..9 wait for the final
+// commit, read the FP32 accumulator with tcgen05.ld (each warp half the columns of its 32-lane
+// quarter) and run the epilogue.  Every mbarrier wait is bounded (2 s of %globaltimer); a wait that gives up
 // sets bit 1 of the status word and the block drains and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -37,7 +37,8 @@ constexpr int kIn = YF_MLP_IN, kWidth = YF_MLP_WIDTH, kOut = YF_MLP_OUT, kLayers
 constexpr int kK1 = 64;        // layer-1 K padded to one 64-wide slice (6 real columns)
 constexpr int kBM = 128;       // rows per tile (tcgen05 M)
 constexpr int kBK = 64;        // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int kThreads = 192;  // producer warp, MMA warp, four epilogue warps
+constexpr int kEpiWarps = 8;   // two per 32-lane quarter of the accumulator, half the columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer warp, MMA warp, epilogue warps
 constexpr long kParams = YF_MLP_PARAMS;
 
 // flat parameter offsets: W_l [out][in] then b_l [out]
@@ -228,7 +229,7 @@ struct GemmSmem {
 };
 
 template <int NT, int kStages>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g)
 {
     using S = GemmSmem<NT, kStages>;
@@ -322,11 +323,14 @@ k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             *abort = 1;
             atomicOr(g.status, 2);
         }
-        const int qtr = warp & 3;
+        // warp w may read TMEM lanes 32 (w % 4) .. +31; the two warps of a quarter split the
+        // columns
+        const int qtr = warp & 3, half = (warp - 2) >> 2;
+        constexpr int NCOL = NT / 2;
         const int row = p0 + 32 * qtr + lane;
         const uint32_t tl = tmem + ((uint32_t)(32 * qtr) << 16);
         // tcgen05.ld is warp-collective: the loop condition must be the same on all lanes
-        for (int c0 = 0; c0 < NT && __all_sync(0xffffffffu, ok && !*abort); c0 += 32) {
+        for (int c0 = half * NCOL; c0 < (half + 1) * NCOL && __all_sync(0xffffffffu, ok && !*abort); c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tl + c0, r);
             const int q = q0 + c0;
@@ -335,7 +339,10 @@ k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
             if (g.mode == MODE_HIDDEN || g.mode == MODE_OUT) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] += __ldg(g.bias + q + i);
+                for (int i = 0; i < 8; ++i) {
+                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + q) + i);
+                    v[4 * i] += b4.x; v[4 * i + 1] += b4.y; v[4 * i + 2] += b4.z; v[4 * i + 3] += b4.w;
+                }
                 if (g.out_f32) {
                     float4 *o = (float4 *)(g.out_f32 + (size_t)row * g.ld_f32 + q);
 #pragma unroll

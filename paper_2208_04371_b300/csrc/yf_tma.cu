@@ -493,9 +493,12 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 }
 
 // Block b takes work item b (instance, tile origin, z-segment); the instance's arguments for
-// the current buffer parity are copied to shared memory behind the TMA layout.
+// the current buffer parity are copied to shared memory behind the TMA layout.  FP32 kinds
+// with one row per thread are held to five resident blocks per SM (the shared-memory limit;
+// 48 registers), the mixed-slab kind to three; FP64 and two-row tiles keep the compiler's
+// choice (a cap would spill).
 template <typename T, int TX, int TYT, int CY, int PM>
-__global__ void __launch_bounds__(TX *TYT)
+__global__ void __launch_bounds__(TX *TYT, (sizeof(T) == 4 && CY == 1) ? ((PM == 7) ? 3 : 5) : 1)
     k_yee_tma_batch(const BatchItem *items, const FusedArgs<T> *args, const CUtensorMap *maps,
                     int parity, int *status)
 {
@@ -552,28 +555,66 @@ template <typename T, int TX, int TYT, int CY>
 cudaError_t launch_plan_t(const TmaPlan &pl, int parity, int *status, cudaStream_t s,
                           const SideStream *side)
 {
-    // kind 0 (no CPML) on the main stream; the CPML kinds on the side stream next to it
+    // kind 0 (no CPML) on the main stream; each CPML kind on its own side stream, so the four
+    // small frame launches overlap one another and the interior
     cudaError_t e;
     const bool frame = pl.count[1] + pl.count[2] + pl.count[3] + pl.count[4] > 0;
-    cudaStream_t fs = s;
-    if (frame && side && side->stream) {
-        if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
-        fs = side->stream;
+    const bool fork = frame && side && side->ready;
+    if (fork && (e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
+    const int kinds[kSideStreams] = {4, 1, 2, 3};
+    bool joined[kSideStreams] = {false, false, false, false};
+    for (int q = 0; q < kSideStreams; ++q) {
+        const int kind = kinds[q];
+        if (pl.count[kind] <= 0) continue;
+        cudaStream_t fs = s;
+        if (fork) {
+            fs = side->stream[q];
+            if ((e = cudaStreamWaitEvent(fs, side->fork, 0)) != cudaSuccess) return e;
+        }
+        switch (kind) {
+        case 4: e = launch_kind<T, TX, TYT, CY, 7>(pl, 4, parity, status, fs); break;
+        case 1: e = launch_kind<T, TX, TYT, CY, 1>(pl, 1, parity, status, fs); break;
+        case 2: e = launch_kind<T, TX, TYT, CY, 2>(pl, 2, parity, status, fs); break;
+        default: e = launch_kind<T, TX, TYT, CY, 4>(pl, 3, parity, status, fs); break;
+        }
+        if (e != cudaSuccess) return e;
+        if (fork) {
+            if ((e = cudaEventRecord(side->join[q], fs)) != cudaSuccess) return e;
+            joined[q] = true;
+        }
     }
-    if ((e = launch_kind<T, TX, TYT, CY, 7>(pl, 4, parity, status, fs)) != cudaSuccess) return e;
-    if ((e = launch_kind<T, TX, TYT, CY, 1>(pl, 1, parity, status, fs)) != cudaSuccess) return e;
-    if ((e = launch_kind<T, TX, TYT, CY, 2>(pl, 2, parity, status, fs)) != cudaSuccess) return e;
-    if ((e = launch_kind<T, TX, TYT, CY, 4>(pl, 3, parity, status, fs)) != cudaSuccess) return e;
     if ((e = launch_kind<T, TX, TYT, CY, 0>(pl, 0, parity, status, s)) != cudaSuccess) return e;
-    if (fs != s) {
-        if ((e = cudaEventRecord(side->join, fs)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
-    }
+    for (int q = 0; q < kSideStreams; ++q)
+        if (joined[q] && (e = cudaStreamWaitEvent(s, side->join[q], 0)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 }  // namespace
+
+cudaError_t side_create(SideStream *s)
+{
+    if (s->ready) return cudaSuccess;
+    cudaError_t e;
+    for (int q = 0; q < kSideStreams; ++q) {
+        if ((e = cudaStreamCreateWithFlags(&s->stream[q], cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s->join[q], cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    s->ready = true;
+    return cudaSuccess;
+}
+
+void side_destroy(SideStream *s)
+{
+    if (!s->ready) return;
+    for (int q = 0; q < kSideStreams; ++q) {
+        cudaStreamSynchronize(s->stream[q]);
+        cudaEventDestroy(s->join[q]);
+        cudaStreamDestroy(s->stream[q]);
+    }
+    cudaEventDestroy(s->fork);
+    s->ready = false;
+}
 
 template <typename T>
 int tma_box_x(int tile_x) { return tile_x + 2 * (16 / (int)sizeof(T)); }

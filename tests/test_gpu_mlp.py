@@ -49,11 +49,11 @@ def cos(a, b):
     return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
-@pytest.mark.parametrize("n", [300, 1, 128])
+@pytest.mark.parametrize("n", [300, 1, 128, 20000])
 def test_forward_matches_oracle(gpu, n):
     flat = W.mlp_init(11, bias_scale=0.1)
     x = raw_inputs(5, n)
-    with gpu.Mlp(1, 128, 512, LO, HI) as m:
+    with gpu.Mlp(1, 128, max(512, n), LO, HI) as m:
         m.set_params(0, flat)
         y, est = m.query(x)
     yo = omlp.forward(tensor_core_view(gpu, flat), mapped_inputs(x))[0]
