@@ -218,6 +218,63 @@ struct GemmArgs {
     int *status;
 };
 
+// Epilogue of 32 accumulator columns of one row: r = FP32 accumulator values of row `row`,
+// columns q .. q + 31 of C.
+__device__ __forceinline__ void epi_chunk(const GemmArgs &g, const uint32_t (&r)[32], int row, int q)
+{
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    if (g.mode == MODE_HIDDEN || g.mode == MODE_OUT) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + q) + i);
+            v[4 * i] += b4.x; v[4 * i + 1] += b4.y; v[4 * i + 2] += b4.z; v[4 * i + 3] += b4.w;
+        }
+        if (g.out_f32) {
+            float4 *o = (float4 *)(g.out_f32 + (size_t)row * g.ld_f32 + q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+        if (g.mode == MODE_OUT) return;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = gelu(v[i]);
+    } else if (g.mode == MODE_DGRAD) {
+        const float4 *zr = (const float4 *)(g.zin + (size_t)row * g.ld_z + q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 z4 = __ldg(zr + i);
+            v[4 * i + 0] *= gelu_grad(z4.x);
+            v[4 * i + 1] *= gelu_grad(z4.y);
+            v[4 * i + 2] *= gelu_grad(z4.z);
+            v[4 * i + 3] *= gelu_grad(z4.w);
+        }
+    } else {   // WGRAD
+        float *o = g.out_f32 + (size_t)row * g.ld_f32;
+        if (q + 32 <= g.qvalid && (g.ld_f32 & 3) == 0) {
+            float4 *o4 = (float4 *)(o + q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        } else {
+            for (int i = 0; i < 32; ++i)
+                if (q + i < g.qvalid) o[q + i] = v[i];
+        }
+        return;
+    }
+    // BF16 row-major copy and transpose (HIDDEN: a, DGRAD: dz)
+    if (g.out_bf) {
+        uint4 *o = (uint4 *)(g.out_bf + (size_t)row * g.ld_bf + q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            o[i] = make_uint4(pack_bf16(v[8 * i + 0], v[8 * i + 1]), pack_bf16(v[8 * i + 2], v[8 * i + 3]),
+                              pack_bf16(v[8 * i + 4], v[8 * i + 5]), pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+    }
+    if (g.out_t) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) g.out_t[(size_t)(q + i) * g.ld_t + row] = __float2bfloat16_rn(v[i]);
+    }
+}
+
 template <int NT, int kStages>
 struct GemmSmem {
     static constexpr int A_BYTES = kBM * kBK * 2;            // 16 KB
@@ -333,58 +390,179 @@ k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
         for (int c0 = half * NCOL; c0 < (half + 1) * NCOL && __all_sync(0xffffffffu, ok && !*abort); c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tl + c0, r);
-            const int q = q0 + c0;
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-            if (g.mode == MODE_HIDDEN || g.mode == MODE_OUT) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + q) + i);
-                    v[4 * i] += b4.x; v[4 * i + 1] += b4.y; v[4 * i + 2] += b4.z; v[4 * i + 3] += b4.w;
+            epi_chunk(g, r, row, q0 + c0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(S::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Persistent form for large grids: one CTA per SM loops over output tiles (row-block major,
+// so the two column tiles of a row block run back to back and share A through L2).  Two FP32
+// accumulators of NT columns live in TMEM: the producer and MMA warps move on to tile t+1
+// while the eight epilogue warps drain tile t, and the MMA warp reuses an accumulator only
+// after all epilogue warps have released it (tmem_empty).  Same operands, epilogue and
+// results as k_mlp_gemm.
+template <int NT>
+struct PersistSmem {
+    static constexpr int ST = 4;
+    static constexpr int A_BYTES = kBM * kBK * 2;
+    static constexpr int B_BYTES = NT * kBK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR_OFF = ST * STAGE;
+    static constexpr int NBAR = 2 * ST + 5;     // full, empty, tmem_full[2], tmem_empty[2], drain
+    static constexpr int BYTES = BAR_OFF + 8 * NBAR + 64 + 1024;
+    static constexpr uint32_t TMEM_COLS = 2 * NT;
+    static_assert(2 * NT <= 512, "two accumulators must fit the 512 TMEM columns");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g)
+{
+    using S = PersistSmem<NT>;
+    constexpr int ST = S::ST;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *sm = smem_raw + (sbase - raw);
+    uint64_t *bars = (uint64_t *)(sm + S::BAR_OFF);
+    volatile uint32_t *tmem_slot = (volatile uint32_t *)(sm + S::BAR_OFF + 8 * S::NBAR);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+    volatile int *consumed = (volatile int *)(tmem_slot + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntn = g.Q / NT, ntiles = (g.P / kBM) * ntn;
+    const int nk = g.R / kBK;
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[ST + s]); };
+    auto tfull = [&](int b) { return smem_u32(&bars[2 * ST + b]); };
+    auto tempty = [&](int b) { return smem_u32(&bars[2 * ST + 2 + b]); };
+    const uint32_t drain = smem_u32(&bars[2 * ST + 4]);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)tmem_slot)),
+                     "r"(S::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto give_up = [&]() {
+        *abort = 1;
+        atomicOr(g.status, 2);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int c = 0;   // running slice count of this CTA: stage c % ST, use c / ST
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+                const int p0 = (t / ntn) * kBM, q0 = (t % ntn) * NT;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = c % ST;
+                    if (c >= ST && !mbar_wait(empty(s), ((c / ST) - 1) & 1, abort)) {
+                        give_up();
+                        break;
+                    }
+                    const uint32_t a_dst = sbase + s * S::STAGE, b_dst = a_dst + S::A_BYTES;
+                    mbar_expect_tx(full(s), S::STAGE);
+                    tma_load_2d(a_dst, &ta, kc * kBK, g.a_row0 + p0, full(s));
+                    tma_load_2d(b_dst, &tb, kc * kBK, g.b_row0 + q0, full(s));
                 }
-                if (g.out_f32) {
-                    float4 *o = (float4 *)(g.out_f32 + (size_t)row * g.ld_f32 + q);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                }
-                if (g.mode == MODE_OUT) continue;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = gelu(v[i]);
-            } else if (g.mode == MODE_DGRAD) {
-                const float4 *zr = (const float4 *)(g.zin + (size_t)row * g.ld_z + q);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 z4 = __ldg(zr + i);
-                    v[4 * i + 0] *= gelu_grad(z4.x);
-                    v[4 * i + 1] *= gelu_grad(z4.y);
-                    v[4 * i + 2] *= gelu_grad(z4.z);
-                    v[4 * i + 3] *= gelu_grad(z4.w);
-                }
-            } else {   // WGRAD
-                float *o = g.out_f32 + (size_t)row * g.ld_f32;
-                if (q + 32 <= g.qvalid && (g.ld_f32 & 3) == 0) {
-                    float4 *o4 = (float4 *)(o + q);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                } else {
-                    for (int i = 0; i < 32; ++i)
-                        if (q + i < g.qvalid) o[q + i] = v[i];
-                }
-                continue;
             }
-            // BF16 row-major copy and transpose (HIDDEN: a, DGRAD: dz)
-            if (g.out_bf) {
-                uint4 *o = (uint4 *)(g.out_bf + (size_t)row * g.ld_bf + q);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    o[i] = make_uint4(pack_bf16(v[8 * i + 0], v[8 * i + 1]), pack_bf16(v[8 * i + 2], v[8 * i + 3]),
-                                      pack_bf16(v[8 * i + 4], v[8 * i + 5]), pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+            if (*abort) {
+                // slices issued but never consumed: let their copies land before exit
+                volatile int keep_waiting = 0;
+                for (int k = *consumed; k < c; ++k) mbar_wait(full(k % ST), (k / ST) & 1, &keep_waiting);
             }
-            if (g.out_t) {
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kBM, NT);
+            int c = 0, it = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++it) {
+                const int b = it & 1;
+                if (it >= 2 && !mbar_wait(tempty(b), ((it >> 1) - 1) & 1, abort)) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * NT);
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = c % ST;
+                    if (!mbar_wait(full(s), (c / ST) & 1, abort)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_s = sbase + s * S::STAGE, b_s = a_s + S::A_BYTES;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) g.out_t[(size_t)(q + i) * g.ld_t + row] = __float2bfloat16_rn(v[i]);
+                    for (int k = 0; k < kBK / 16; ++k)
+                        mma_bf16(acc, sw128_desc(a_s + 32 * k), sw128_desc(b_s + 32 * k), idesc, (kc | k) != 0);
+                    mma_commit(empty(s));
+                    *consumed = c + 1;
+                }
+                if (!ok) break;
+                mma_commit(tfull(b));
             }
+            // every MMA issued so far has completed once this arrives; TMEM may then be freed
+            mma_commit(drain);
+            volatile int keep_waiting = 0;
+            mbar_wait(drain, 0, &keep_waiting);
+        }
+    } else {
+        const int qtr = warp & 3, half = (warp - 2) >> 2;
+        constexpr int NCOL = NT / 2;
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const bool ok = mbar_wait(tfull(b), (it >> 1) & 1, abort);
+            if (__any_sync(0xffffffffu, !ok)) {
+                if (lane == 0) give_up();
+                break;
+            }
+            tc_fence_after();
+            const int p0 = (t / ntn) * kBM, q0 = (t % ntn) * NT;
+            const int row = p0 + 32 * qtr + lane;
+            const uint32_t tl = tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(b * NT);
+            for (int c0 = half * NCOL; c0 < (half + 1) * NCOL; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tl + c0, r);
+                epi_chunk(g, r, row, q0 + c0);
+            }
+            // this warp's reads of accumulator b are complete: release it to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(b));
         }
     }
     tc_fence_before();
@@ -663,6 +841,25 @@ yf_status dalloc(yf_mlp *m, T **p, size_t count)
     return YF_OK;
 }
 
+template <int NT>
+cudaError_t prepare_persist()
+{
+    return cudaFuncSetAttribute(k_mlp_gemm_persist<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PersistSmem<NT>::BYTES);
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 148;
+    }
+    return n;
+}
+
 template <int NT, int ST>
 cudaError_t prepare_gemm()
 {
@@ -685,7 +882,11 @@ cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmAr
 {
     if (g.Q % 256 == 0) {
         const long tiles = (long)(g.P / kBM) * (g.Q / 256);
-        if (tiles >= 2 * 148) return launch_gemm_t<256, 2>(a, b, g, s);
+        if (tiles >= 2 * sm_count()) {
+            // persistent: one CTA per SM (its shared memory admits no second one)
+            k_mlp_gemm_persist<256><<<sm_count(), kThreads, PersistSmem<256>::BYTES, s>>>(a, b, g);
+            return cudaGetLastError();
+        }
         return launch_gemm_t<256, 4>(a, b, g, s);
     }
     return launch_gemm_t<64, 4>(a, b, g, s);
@@ -828,8 +1029,8 @@ yf_status yf_mlp_create(int members, int train_batch, int max_query, const doubl
             return bail(cuda_fail(cudaGetLastError(), "cudaStreamCreateWithFlags"));
         m->own_stream = true;
     }
-    if (prepare_gemm<256, 2>() != cudaSuccess || prepare_gemm<256, 4>() != cudaSuccess ||
-        prepare_gemm<64, 4>() != cudaSuccess)
+    if (prepare_gemm<256, 4>() != cudaSuccess || prepare_gemm<64, 4>() != cudaSuccess ||
+        prepare_persist<256>() != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaFuncSetAttribute(k_mlp_gemm)"));
     yf_status st;
 #define TRY(x)                                \
