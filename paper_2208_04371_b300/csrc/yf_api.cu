@@ -767,6 +767,13 @@ yf_status yf_write_fields(yf_grid *g, int comp, const void *src, yf_mem where)
         e = launch_sanitize<double>(fields_of<double>(g, g->cur), g->cls, g->nx, g->ny, g->nz, g->px,
                                     g->plane, g->stream);
     YF_CUDA_TRY(e);
+    // both field buffers carry the written component: the TMA-staged step skips the node
+    // column i = nx and row j = ny when they form a tile of their own, and there the two
+    // buffers must already agree (only H_x at i = nx and H_y at j = ny live there, and the
+    // update leaves them unchanged: their tangential E neighbours are PEC)
+    const size_t bytes = (size_t)g->npts * g->esz;
+    YF_CUDA_TRY(cudaMemcpyAsync((char *)g->buf[g->cur ^ 1] + (size_t)comp * bytes, g->fld(comp), bytes,
+                                cudaMemcpyDeviceToDevice, g->stream));
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     return YF_OK;
 }
@@ -1063,6 +1070,9 @@ yf_status yf_checkpoint_load(yf_grid *g, const char *path)
     load(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));
     fclose(fp);
     if (!ok) return fail(YF_E_INVALID, "checkpoint %s is truncated", path);
+    // the other field buffer must agree on the nodes a step leaves untouched
+    YF_CUDA_TRY(cudaMemcpy(g->buf[g->cur ^ 1], g->buf[g->cur], 6 * g->npts * g->esz,
+                           cudaMemcpyDeviceToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->ctr, &h.ctr, sizeof(long long), cudaMemcpyHostToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->status, &h.status, sizeof(int), cudaMemcpyHostToDevice));
     g->steps_done = h.steps;

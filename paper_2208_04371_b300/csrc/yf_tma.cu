@@ -650,8 +650,13 @@ cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *stat
 void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
                const int hi[3], std::vector<BatchItem> items[5])
 {
+    // Tiles cover node columns 0 .. nx-1 and rows 0 .. ny-1.  The last node column i = nx
+    // (and row j = ny) joins a tile only when nx (ny) is not a multiple of the tile: on that
+    // PEC-backed face the tangential E are zero and the only H there (H_x at i = nx, H_y at
+    // j = ny) keeps its value, so a tile holding nothing else is skipped (the two field
+    // buffers hold equal values there: the write and checkpoint-load calls fill both).
     const int TX = 32, TY = tile_y;
-    const int ntx = (nx + 1 + TX - 1) / TX, nty = (ny + 1 + TY - 1) / TY;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
     const bool hp = n > 0 && (lo[0] || hi[0] || lo[1] || hi[1] || lo[2] || hi[2]);
     auto lo_tile = [](int on, int n_, int tile) { return on ? (n_ + 1 + tile - 1) / tile : 0; };
     auto hi_tile = [](int on, int N, int n_, int tile, int count) {
