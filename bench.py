@@ -37,6 +37,21 @@ def workload(nz: int = 256):
     return W.config_lossy_line(nz=nz, nsteps=0)
 
 
+def stencil_traffic():
+    """DRAM bytes per step of the stencil from the committed ncu capture, or None when the
+    stencil source has changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_yee_tma_batch_traffic_lossy_line_768x384x256.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    for rel, digest in d["source_sha256"].items():
+        f = os.path.join(ROOT, rel)
+        if not os.path.exists(f) or hashlib.sha256(open(f, "rb").read()).hexdigest() != digest:
+            return None
+    return d["dram_bytes_per_step"]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -283,7 +298,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = BYTES_PER_CELL_FP32 * p.cells / (stencil_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak,
+            "traffic": stencil_traffic() if (args.nz == 256 and kname == "k_yee_tma_batch") else None,
+            "traffic_unit": "bytes per step (all work kinds)",
             "bytes_per_cell_update": BYTES_PER_CELL_FP32,
             "kernel_ms": prof}
 

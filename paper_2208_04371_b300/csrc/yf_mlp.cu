@@ -220,7 +220,8 @@ struct GemmArgs {
 
 // Epilogue of 32 accumulator columns of one row: r = FP32 accumulator values of row `row`,
 // columns q .. q + 31 of C.
-__device__ __forceinline__ void epi_chunk(const GemmArgs &g, const uint32_t (&r)[32], int row, int q)
+__device__ __forceinline__ void epi_chunk(const GemmArgs &g, const uint32_t (&r)[32], int row, int q,
+                                          const float *bias)
 {
     float v[32];
 #pragma unroll
@@ -228,7 +229,7 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs &g, const uint32_t (&r)
     if (g.mode == MODE_HIDDEN || g.mode == MODE_OUT) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + q) + i);
+            const float4 b4 = reinterpret_cast<const float4 *>(bias + q)[i];
             v[4 * i] += b4.x; v[4 * i + 1] += b4.y; v[4 * i + 2] += b4.z; v[4 * i + 3] += b4.w;
         }
         if (g.out_f32) {
@@ -390,7 +391,7 @@ k_mlp_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
         for (int c0 = half * NCOL; c0 < (half + 1) * NCOL && __all_sync(0xffffffffu, ok && !*abort); c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tl + c0, r);
-            epi_chunk(g, r, row, q0 + c0);
+            epi_chunk(g, r, row, q0 + c0, g.bias);
         }
     }
     tc_fence_before();
@@ -417,7 +418,10 @@ struct PersistSmem {
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int BAR_OFF = ST * STAGE;
     static constexpr int NBAR = 2 * ST + 5;     // full, empty, tmem_full[2], tmem_empty[2], drain
-    static constexpr int BYTES = BAR_OFF + 8 * NBAR + 64 + 1024;
+    // bias of all Q <= 512 columns, read as float4: 16-byte (here 128-byte) aligned
+    static constexpr int BIAS_OFF = (BAR_OFF + 8 * NBAR + 64 + 127) / 128 * 128;
+    static constexpr int BYTES = BIAS_OFF + 4 * 512 + 1024;
+    static_assert(BIAS_OFF % 16 == 0, "float4 reads of the staged bias");
     static constexpr uint32_t TMEM_COLS = 2 * NT;
     static_assert(2 * NT <= 512, "two accumulators must fit the 512 TMEM columns");
 };
@@ -542,6 +546,12 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
     } else {
         const int qtr = warp & 3, half = (warp - 2) >> 2;
         constexpr int NCOL = NT / 2;
+        // the layer's bias, once per CTA, for every tile's epilogue (named barrier 1: the
+        // epilogue warps only)
+        float *sbias = reinterpret_cast<float *>(sm + S::BIAS_OFF);
+        if (g.bias)
+            for (int c = threadIdx.x - 64; c < g.Q; c += 32 * kEpiWarps) sbias[c] = __ldg(g.bias + c);
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
         int it = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const int b = it & 1;
@@ -557,7 +567,7 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
             for (int c0 = half * NCOL; c0 < (half + 1) * NCOL; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tl + c0, r);
-                epi_chunk(g, r, row, q0 + c0);
+                epi_chunk(g, r, row, q0 + c0, sbias);
             }
             // this warp's reads of accumulator b are complete: release it to the MMA warp
             tc_fence_before();
