@@ -84,14 +84,22 @@ __global__ void k_collect(KeyArgs A, uint32_t *table, int *overflow)
         if (i > A.nx || j > A.ny) continue;
         for (int comp = 0; comp < 3; ++comp) {
             const uint32_t key = edge_key(A, comp, i, j, k);
-            if (key == kEmpty) continue;
+            // a handful of distinct keys among millions of edges: one lane per distinct key
+            // of the warp inserts, and a slot is read before any compare-and-swap, so the set
+            // fills with a few atomics instead of one contended atomic per edge
+            const unsigned active = __activemask();
+            const unsigned peers = __match_any_sync(active, key);
+            if (key == kEmpty || (int)(__ffs(peers) - 1) != (int)(threadIdx.x & 31)) continue;
             uint32_t s = hash_slot(key);
-            int probes = 0;
-            while (true) {
-                const uint32_t prev = atomicCAS(&table[s], kEmpty, key);
-                if (prev == kEmpty || prev == key) break;
+            for (int probes = 0;; ++probes) {
+                if (probes >= kHashSize) { atomicOr(overflow, 1); break; }
+                const uint32_t cur = *(volatile const uint32_t *)&table[s];
+                if (cur == key) break;
+                if (cur == kEmpty) {
+                    const uint32_t prev = atomicCAS(&table[s], kEmpty, key);
+                    if (prev == kEmpty || prev == key) break;
+                }
                 s = (s + 1) & (kHashSize - 1);
-                if (++probes >= kHashSize) { atomicOr(overflow, 1); break; }
             }
         }
     }
