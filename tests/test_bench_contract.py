@@ -1,0 +1,44 @@
+"""Host-side pieces of bench.py: the reference arm's JSON line (the oracle on a bounded
+sample) and the rule that the stored stencil traffic is dropped once the stencil changes."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--ref-seconds", "2"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_stored_traffic_is_dropped_when_the_stencil_changes(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.stencil_traffic() is not None          # committed capture matches the source
+    # a copy of the tree whose stencil source differs by one byte
+    fake = tmp_path / "root"
+    (fake / "profiles").mkdir(parents=True)
+    (fake / "paper_2208_04371_b300" / "csrc").mkdir(parents=True)
+    name = "k_yee_tma_batch_traffic_lossy_line_768x384x256.json"
+    shutil.copy(os.path.join(ROOT, "profiles", name), fake / "profiles" / name)
+    src = open(os.path.join(ROOT, "paper_2208_04371_b300", "csrc", "yf_tma.cu"), "rb").read()
+    (fake / "paper_2208_04371_b300" / "csrc" / "yf_tma.cu").write_bytes(src + b"\n")
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    assert bench.stencil_traffic() is None
