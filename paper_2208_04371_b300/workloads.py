@@ -239,6 +239,26 @@ def config_long_run(nsteps: int = 1_000_000, ringing: bool = False, nfreq: int =
                       name="long-run 256x128x128" + (" ringing" if ringing else ""))
 
 
+def config_microstrip_theory(nsteps: int = 60_000, nfreq: int = 128) -> Problem:
+    """The paper's verification microstrip (Sec. II-B) in this build's frame (propagation
+    along x): 1000 x 200 x 50 cells of 0.1 mm; SiO2 substrate (eps_r 3.8) 1 mm = 10 cells
+    thick; zero-thickness PEC strip 57 cells wide (w/h = 5.7, designed for 25 ohm); CFL 0.9;
+    Eq. 3 differential Gaussian, sigma = 11.254 ps, t0 = 3 sigma; 60000 steps.  8-cell PML on
+    the x ends, y sides and top, PEC ground; source plane 10, ports at 30 and 970 (94 mm
+    apart); 128 DFT frequencies over 0.2-40 GHz (the lowest keeps beta l under pi, so the
+    phase of S*_21 unwraps from the first frequency; 60000 steps resolve about 0.1 GHz)."""
+    nx, ny, nz, sub, w = 1000, 200, 50, 10, 57
+    j0 = (ny - w) // 2
+    prob = microstrip(nx, ny, nz, 1e-4, sub_cells=sub, strip_j0=j0, strip_j1=j0 + w, eps_r=3.8,
+                      sigma=0.0, pml=8, bc=(BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML),
+                      courant=0.9, nsteps=nsteps, freqs=linear_freqs(0.2e9, 40e9, nfreq),
+                      f0=20e9, bw=20e9, src_plane=10, port_planes=(30, nx - 30),
+                      name="paper microstrip 1000x200x50 0.1mm")
+    prob.source = Source(kind=WAVE_DIFF_GAUSS, plane=10, j0=j0, j1=j0 + w, k0=0, k1=sub,
+                         amplitude=1.0, param0=11.254e-12)
+    return prob
+
+
 SURROGATE_LO = (4.0, 0.0, 6.0, 2.0, 0.0, 32.0)
 SURROGATE_HI = (40.0, 10.0, 30.0, 12.0, 50.0, 160.0)
 

@@ -1,0 +1,64 @@
+"""The paper's microstrip verification (Sec. II-B) at full size on the GPU: a 25-ohm lossless
+line (w/h = 5.7, eps_r = 3.8, 1 mm SiO2, 0.1 mm cells, 60000 steps) between 50-ohm ports,
+against the transmission-line closed forms (Eq. 7 and C_th = 1/(Z0 v), L_th = Z0 / v).
+
+Physics-level and loose. The FDTD line is the discretised structure: a zero-thickness strip,
+a finite air box, 10 cells across the substrate. The closed forms are quasi-TEM, so they hold
+while the strip is small against the guided wavelength. Bands:
+  quasi-static, f <= 3 GHz (w < lambda_g / 10):
+    eps_eff from the phase delay (Eq. 8) within 3 % of Hammerstad-Jensen (3.19);
+    C and L per unit length within 10 % of C_th, L_th (quasi-static quantities);
+    |S11|^2 + |S21|^2 = 1 within 5e-2: the line is lossless, but the waves come from V
+    (strip-centre surface integral) and I (loop one cell out), which are not exact power
+    waves for a quasi-TEM mode with fringing fields (measured 0.991-1.032).
+  quasi-TEM, f <= 15 GHz:
+    Z_c within 10 % of 25.1 ohm;
+    Eq. 7 with the line's own Gamma = (Z_c - 50)/(Z_c + 50) and kappa = exp(-j beta l)
+    (beta from the phase delay) reproduces the extracted S within 0.08 (measured 0.039 on
+    S11, 0.057 on S21; the same V/I-wave effect);
+    the largest |S11| (sampled) lies between 0.5 and 0.65, around 2|G|/(1 + G^2) = 0.6.
+At higher frequencies the microstrip disperses (eps_eff rises to 3.67 at 38 GHz) and the
+box supports non-TEM fields; there the closed forms are not expected to hold."""
+import numpy as np
+import pytest
+
+from oracle import post
+from paper_2208_04371_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C0 = 299792458.0
+
+
+def test_paper_microstrip_matches_transmission_line_theory(gpu):
+    p = W.config_microstrip_theory()
+    with gpu.Grid(p, prec=gpu.FP32) as g:
+        assert g.dt == pytest.approx(0.173e-12, rel=2e-3)       # Sec. II-B's printed step
+        g.step(p.nsteps)
+        g.sync()
+        sp = g.sparams()
+    f = p.freqs
+    static, tem = f <= 3e9, f <= 15e9
+    z0_hj, eeff_hj = post.microstrip_z0_hammerstad(5.7, 3.8)
+    zc = sp["Zc"]
+    l = (p.ports[1].plane - p.ports[0].plane) * p.dx
+    v = l / sp["tau"][:, 1, 0]
+    eeff = (C0 / v) ** 2
+    assert np.all(np.abs(eeff[static] - eeff_hj) <= 0.03 * eeff_hj), eeff[static]
+    S = sp["S"]
+    power = np.abs(S[:, 0, 0]) ** 2 + np.abs(S[:, 1, 0]) ** 2
+    assert np.all(np.abs(power[static] - 1.0) <= 5e-2), power[static]
+
+    assert np.all(np.abs(zc[tem].real - z0_hj) <= 0.10 * z0_hj), zc[tem].real
+    v_th = C0 / np.sqrt(eeff_hj)
+    c_fd, l_fd = 1.0 / (zc.real * v), zc.real / v
+    c_th, l_th = 1.0 / (z0_hj * v_th), z0_hj / v_th
+    assert np.all(np.abs(c_fd[static] - c_th) <= 0.10 * c_th)
+    assert np.all(np.abs(l_fd[static] - l_th) <= 0.10 * l_th)
+
+    gam = (zc.real - 50.0) / (zc.real + 50.0)
+    kappa = np.exp(-2j * np.pi * f * sp["tau"][:, 1, 0])       # beta l = 2 pi f tau
+    s11, s21 = post.lossless_line_s(kappa, gam)
+    assert np.max(np.abs(s11[tem] - S[tem, 0, 0])) <= 0.08
+    assert np.max(np.abs(s21[tem] - S[tem, 1, 0])) <= 0.08
+    assert 0.5 <= np.max(np.abs(S[tem, 0, 0])) <= 0.65
