@@ -109,3 +109,48 @@ def test_unwrap_handles_multiple_turns():
     ph = np.linspace(0, -1500.0, 400)
     wrapped = (ph + 180.0) % 360.0 - 180.0
     assert np.allclose(post.unwrap_deg(wrapped), ph, atol=1e-9)
+
+
+def _line_sstar(R, L, G, C, length, freqs, zr):
+    """S* of a uniform line of known per-unit-length R, L, G, C between real references zr,
+    built from its ABCD matrix (cosh, sinh of gamma l) through the impedance matrix and the
+    pseudo-wave relation S = (Zn - I)(Zn + I)^{-1}, Zn = R^{-1} Z R^{-1} (written here, not
+    taken from the module under test)."""
+    w = 2 * np.pi * freqs
+    zs, yp = R + 1j * w * L, G + 1j * w * C
+    gam, zc = np.sqrt(zs * yp), np.sqrt(zs / yp)
+    out = np.zeros((len(freqs), 2, 2), complex)
+    for f in range(len(freqs)):
+        ch, sh = np.cosh(gam[f] * length), np.sinh(gam[f] * length)
+        A, B, Cm, D = ch, zc[f] * sh, sh / zc[f], ch
+        Z = np.array([[A / Cm, (A * D - B * Cm) / Cm], [1 / Cm, D / Cm]])
+        Rn = np.diag(1 / np.sqrt(zr))
+        Zn = Rn @ Z @ Rn
+        out[f] = (Zn - np.eye(2)) @ np.linalg.inv(Zn + np.eye(2))
+    return out
+
+
+def test_rlcg_recovers_a_lossy_line():
+    freqs = np.linspace(0.1e9, 20e9, 64)
+    R, L, G, C, length = 5.0, 3.0e-7, 1.0e-3, 1.2e-10, 0.05
+    zr = np.array([40.0, 60.0])
+    S = _line_sstar(R, L, G, C, length, freqs, zr)
+    out = post.rlcg(S, np.repeat(zr[:, None], len(freqs), axis=1), freqs, length)
+    assert np.allclose(out["R"], R, rtol=1e-8)
+    assert np.allclose(out["L"], L, rtol=1e-10)
+    assert np.allclose(out["G"], G, rtol=1e-7)
+    assert np.allclose(out["C"], C, rtol=1e-10)
+    assert np.allclose(out["Zc"], np.sqrt((R + 2j * np.pi * freqs * L) / (G + 2j * np.pi * freqs * C)),
+                       rtol=1e-10)
+
+
+def test_rlcg_of_a_lossless_line_has_no_loss_terms():
+    freqs = np.linspace(0.2e9, 30e9, 80)
+    # beta l reaches 78 rad (unwrapping needed) and stays off multiples of pi, where
+    # sinh(gamma l) = 0 and the ABCD matrix carries no Z_c
+    L, C, length = 2.5e-7, 1.0e-10, 0.083
+    S = _line_sstar(0.0, L, 0.0, C, length, freqs, np.array([50.0, 50.0]))
+    out = post.rlcg(S, np.full((2, len(freqs)), 50.0), freqs, length)
+    w = 2 * np.pi * freqs
+    assert np.all(np.abs(out["R"]) <= 1e-8 * w * L) and np.all(np.abs(out["G"]) <= 1e-8 * w * C)
+    assert np.allclose(out["L"], L, rtol=1e-10) and np.allclose(out["C"], C, rtol=1e-10)
