@@ -234,6 +234,21 @@ yf_status yf_sparams_noalloc(int nports, int nfreq, const double *freqs, const d
                              double *S_star, double *S, double *Zr, double *Zc, double *tau,
                              void *stream);
 
+/* Telegrapher's model of a two-port (end of Sec. II-A): per-unit-length R [ohm/m], L [H/m],
+ * G [S/m], C [F/m] and, when gamma is non-NULL, the propagation constant gamma [1/m]
+ * (complex interleaved, [F]) of a line of physical length `length` [m].
+ *   S_star [F][2][2] and Zr [2][F]: host arrays, complex interleaved (as yf_sparams returns).
+ *   S* -> Z (pseudo-waves with the port references) -> ABCD; gamma l = +-acosh((A + D)/2)
+ *   + 2 pi j k.  acosh folds beta l into [0, pi], so the branch is continued from the lowest
+ *   frequency (which must have beta l < pi, as for Eq. 8) along beta l ~ f, and alpha's sign
+ *   follows from beta > 0; Z_c = sqrt(B/C), Re >= 0; R + j w L = gamma Z_c,
+ *   G + j w C = gamma / Z_c.  Frequencies must be positive and increasing.  A frequency where
+ *   the conversion is singular (I - S* not invertible, e.g. a matched lossless line at
+ *   beta l = m pi) gives NaN there only.
+ * FP64 on the GPU; synchronous. */
+yf_status yf_rlcg(int nfreq, const double *freqs, const double *S_star, const double *Zr,
+                  double length, double *gamma, double *R, double *L, double *G, double *C);
+
 /* Uniform-line shortcut for a two-port grid driven at port 0 (incident and total runs
  * coincide; S*_11 = S*_22 = 0, S*_12 = S*_21; port 1's Z_r from the same forward wave).
  * Uses the FP64 accumulators and port 0's frequency list. */

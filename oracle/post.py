@@ -145,41 +145,41 @@ def zc_from_sstar(S_star: np.ndarray, Zr: np.ndarray) -> np.ndarray:
 
 def rlcg(S_star: np.ndarray, Zr: np.ndarray, freqs: np.ndarray, length: float) -> dict:
     """Telegrapher's model of a two-port (end of Sec. II-A): S* -> Z -> ABCD, then
-    gamma l = acosh((A + D) / 2) with Re >= 0 and the imaginary part continued from the
-    lowest frequency (which must have beta l < pi, as for Eq. 8) along beta l ~ f (acosh
-    folds beta l into [0, pi], so each branch is the one nearest that trend), Z_c = sqrt(B / C) with
-    Re >= 0, and per unit length R + j w L = gamma Z_c, G + j w C = gamma / Z_c."""
+    gamma l = +-acosh((A + D) / 2) + 2 pi j k (cosh is even and periodic).  The lowest
+    frequency takes beta l in [0, pi] (it must lie below pi, as for Eq. 8); every further
+    frequency takes the candidate nearest the line's trend, beta l grown in proportion to f
+    from the last frequency with a finite result (acosh folds beta l into [0, pi]).  The sign
+    of alpha follows from beta > 0.  Z_c = sqrt(B / C) with Re >= 0; per unit length
+    R + j w L = gamma Z_c, G + j w C = gamma / Z_c.  Where the conversion is singular (I - S*
+    not invertible: a matched lossless line at beta l = m pi) the results are NaN."""
     F = S_star.shape[0]
-    gl = np.zeros(F, dtype=np.complex128)
-    zc = np.zeros(F, dtype=np.complex128)
-    prev = None
+    gl = np.full(F, np.nan + 0j)
+    zc = np.full(F, np.nan + 0j)
+    prev, fprev = None, None
     for f in range(F):
-        Z = zmatrix(S_star[f], Zr[:, f])
-        A, Bm, Cm, D = (Z[0, 0] / Z[1, 0], (Z[0, 0] * Z[1, 1] - Z[0, 1] * Z[1, 0]) / Z[1, 0],
-                        1.0 / Z[1, 0], Z[1, 1] / Z[1, 0])
-        z = np.sqrt(Bm / Cm)
+        with np.errstate(all="ignore"):
+            try:
+                Z = zmatrix(S_star[f], Zr[:, f])
+            except np.linalg.LinAlgError:
+                continue
+            A, Bm, Cm, D = (Z[0, 0] / Z[1, 0], (Z[0, 0] * Z[1, 1] - Z[0, 1] * Z[1, 0]) / Z[1, 0],
+                            1.0 / Z[1, 0], Z[1, 1] / Z[1, 0])
+            z = np.sqrt(Bm / Cm)
+            g = np.arccosh(0.5 * (A + D))
+        if not (np.isfinite(g) and np.isfinite(z)):
+            continue
         zc[f] = z if z.real >= 0 else -z
-        g = np.arccosh(0.5 * (A + D))
-        if g.real < 0:
-            g = -g
-        # cosh is even: +-g and g + 2 pi j k all fit.  Re >= 0 (a passive line attenuates);
-        # when Re is at roundoff (a lossless line) the conjugate is admissible too
-        cands = [g]
-        if abs(g.real) <= 1e-9 * abs(g):
-            cands.append(complex(abs(g.real), -g.imag))
-        if prev is None:       # lowest frequency: beta l in [0, pi)
-            g = max(cands, key=lambda c: c.imag)
+        if prev is None:
+            g = g if (g.imag > 0 or (g.imag == 0 and g.real >= 0)) else -g
         else:
-            # acosh folds beta l into [0, pi]: pick the branch nearest the line's own trend,
-            # beta l growing in proportion to f from the previous frequency
-            pred = prev.imag * freqs[f] / freqs[f - 1]
+            pred = prev.imag * freqs[f] / fprev
             best = None
-            for c in cands:
+            for c in (g, -g):
                 c = c + 2j * np.pi * np.round((pred - c.imag) / (2 * np.pi))
                 if best is None or abs(c.imag - pred) < abs(best.imag - pred):
                     best = c
             g = best
-        prev = g
+        prev, fprev = g, freqs[f]
         gl[f] = g
     gamma = gl / length
     w = 2 * np.pi * freqs

@@ -37,11 +37,12 @@ __device__ __forceinline__ cplx dvd(cplx a, cplx b)
     return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
 }
 __device__ __forceinline__ double cabs_(cplx a) { return hypot(a.re, a.im); }
-// principal square root
+// principal square root; both radicands are clamped at zero, because |z| rounded by hypot
+// can fall an ulp below |Re z| for an (almost) real argument
 __device__ __forceinline__ cplx csqrt_(cplx z)
 {
     const double r = cabs_(z);
-    const double a = sqrt(0.5 * (r + z.re));
+    const double a = sqrt(0.5 * fmax(r + z.re, 0.0));
     const double b = sqrt(0.5 * fmax(r - z.re, 0.0));
     return {a, z.im < 0 ? -b : b};
 }
@@ -197,6 +198,82 @@ __global__ void k_phase_delay(const cplx *sstar, const double *freqs, int n, int
     }
 }
 
+// principal complex logarithm and inverse hyperbolic cosine, acosh z = log(z + sqrt(z+1) sqrt(z-1))
+__device__ __forceinline__ cplx clog_(cplx z) { return {log(cabs_(z)), atan2(z.im, z.re)}; }
+__device__ __forceinline__ cplx cacosh_(cplx z)
+{
+    return clog_(add(z, mul(csqrt_(add(z, mk(1, 0))), csqrt_(sub(z, mk(1, 0))))));
+}
+
+// Telegrapher's model of a two-port (end of Sec. II-A): S* -> Z (pseudo-waves with the port
+// references) -> ABCD; gamma l = +-acosh((A + D)/2) + 2 pi j k (cosh is even and periodic).
+// acosh folds beta l into [0, pi], so one thread walks the frequencies in order: the lowest
+// takes beta l in [0, pi], every further one the candidate nearest beta l grown in proportion
+// to f from the last frequency with a finite result; alpha's sign follows from beta > 0.
+// Z_c = sqrt(B/C) with Re >= 0; R + j w L = gamma Z_c, G + j w C = gamma / Z_c per unit length.
+// A singular conversion (I - S* not invertible) gives NaN at that frequency only.
+__global__ void k_rlcg(const cplx *sstar, const cplx *zr, const double *freqs, int nf, double length,
+                       cplx *gamma, double *R, double *L, double *G, double *C)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double twopi = 6.283185307179586476925286766559;
+    cplx prev = mk(0, 0);
+    double fprev = 0.0;
+    bool have = false;
+    for (int f = 0; f < nf; ++f) {
+        cplx S[4], P[4], Pi[4];
+        for (int q = 0; q < 4; ++q) S[q] = sstar[(size_t)f * 4 + q];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) P[r * 2 + c] = sub(mk(r == c ? 1.0 : 0.0, 0.0), S[r * 2 + c]);
+        cplx g = mk(NAN, NAN), zc = mk(NAN, NAN);
+        if (inverse(P, Pi, 2)) {
+            const cplx rt[2] = {csqrt_(zr[f]), csqrt_(zr[nf + f])};
+            cplx Z[4];
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) {
+                    cplx m = mk(0, 0);
+                    for (int q = 0; q < 2; ++q)
+                        m = add(m, mul(add(mk(r == q ? 1.0 : 0.0, 0.0), S[r * 2 + q]), Pi[q * 2 + c]));
+                    Z[r * 2 + c] = mul(mul(rt[r], m), rt[c]);
+                }
+            const cplx A = dvd(Z[0], Z[2]), D = dvd(Z[3], Z[2]);
+            const cplx Bm = dvd(sub(mul(Z[0], Z[3]), mul(Z[1], Z[2])), Z[2]);
+            const cplx Cm = dvd(mk(1, 0), Z[2]);
+            zc = csqrt_(dvd(Bm, Cm));
+            if (zc.re < 0) zc = mk(-zc.re, -zc.im);
+            g = cacosh_(mk(0.5 * (A.re + D.re), 0.5 * (A.im + D.im)));
+        }
+        const bool finite = isfinite(g.re) && isfinite(g.im) && isfinite(zc.re) && isfinite(zc.im);
+        if (finite) {
+            if (!have) {
+                if (!(g.im > 0 || (g.im == 0 && g.re >= 0))) g = mk(-g.re, -g.im);
+            } else {
+                const double pred = prev.im * freqs[f] / fprev;
+                const cplx cand[2] = {g, mk(-g.re, -g.im)};
+                for (int q = 0; q < 2; ++q) {
+                    const cplx c = cand[q];
+                    const cplx cs = mk(c.re, c.im + twopi * rint((pred - c.im) / twopi));
+                    if (q == 0 || fabs(cs.im - pred) < fabs(g.im - pred)) g = cs;
+                }
+            }
+            prev = g;
+            fprev = freqs[f];
+            have = true;
+        } else {
+            g = mk(NAN, NAN);
+            zc = mk(NAN, NAN);
+        }
+        const cplx gam = mk(g.re / length, g.im / length);
+        const cplx zs = mul(gam, zc), yp = dvd(gam, zc);
+        const double w = twopi * freqs[f];
+        if (gamma) gamma[f] = gam;
+        R[f] = zs.re;
+        L[f] = zs.im / w;
+        G[f] = yp.re;
+        C[f] = yp.im / w;
+    }
+}
+
 yf_status run_sparams(int n, int nf, const double *freqs, const std::vector<double> &vinc,
                       const std::vector<double> &iinc, const std::vector<double> &vtot, int uniform,
                       int dir1, double z_ref, double *S_star, double *S, double *Zr, double *Zc,
@@ -290,6 +367,44 @@ extern "C" yf_status yf_sparams(int nports, int nfreq, const double *freqs, cons
         }
     }
     return run_sparams(n, nf, freqs, vinc, iinc, vtot, 0, 1, z_ref, S_star, S, Zr, Zc, tau);
+}
+
+extern "C" yf_status yf_rlcg(int nfreq, const double *freqs, const double *S_star, const double *Zr,
+                             double length, double *gamma, double *R, double *L, double *G, double *C)
+{
+    using namespace yf;
+    if (nfreq < 1 || !freqs || !S_star || !Zr || !R || !L || !G || !C || !(length > 0))
+        return fail(YF_E_INVALID, "yf_rlcg: bad arguments");
+    for (int f = 0; f < nfreq; ++f)
+        if (!(freqs[f] > 0) || (f > 0 && !(freqs[f] > freqs[f - 1])))
+            return fail(YF_E_INVALID, "yf_rlcg: frequencies must be positive and increasing");
+    const int nf = nfreq;
+    // device staging: S* [F][4], Zr [2][F] (complex), freqs [F], outputs gamma [F] + 4 x [F]
+    const size_t in_c = (size_t)6 * nf, out_d = (size_t)2 * nf + 4 * (size_t)nf;
+    double *buf = nullptr;
+    YF_CUDA_TRY(cudaMalloc(&buf, (2 * in_c + nf + out_d) * sizeof(double)));
+    cplx *ds = (cplx *)buf, *dz = ds + 4 * nf;
+    double *dfq = buf + 2 * in_c, *dout = dfq + nf;
+    cudaError_t e = cudaMemcpy(ds, S_star, (size_t)4 * nf * sizeof(cplx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dz, Zr, (size_t)2 * nf * sizeof(cplx), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dfq, freqs, nf * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_rlcg<<<1, 1>>>(ds, dz, dfq, nf, length, (cplx *)dout, dout + 2 * nf, dout + 3 * nf,
+                         dout + 4 * nf, dout + 5 * nf);
+        e = cudaGetLastError();
+    }
+    std::vector<double> h(out_d);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), dout, out_d * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "yf_rlcg");
+    if (gamma) for (size_t q = 0; q < 2 * (size_t)nf; ++q) gamma[q] = h[q];
+    for (int f = 0; f < nf; ++f) {
+        R[f] = h[2 * nf + f];
+        L[f] = h[3 * nf + f];
+        G[f] = h[4 * nf + f];
+        C[f] = h[5 * nf + f];
+    }
+    return YF_OK;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -102,6 +102,7 @@ _SIGS = {
     "yf_read_sparams_acc": (_i, [_vp, _i, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_launches_per_step": (_i, [_vp, C.POINTER(_i)]),
     "yf_bounded_wait_check": (_i, [_i, _d]),
+    "yf_rlcg": (_i, [_i, _dp, _dp, _dp, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
     "yf_set_variant": (_i, [_vp, _i, _i, _i]),
@@ -349,6 +350,20 @@ def read_sparams(g, nfreq, z_ref=50.0, kind=DFT_FP64):
                                         tau.ctypes.data_as(_dp)))
     return dict(S_star=_as_complex(ss), S=_as_complex(s), Zr=_as_complex(zr), Zc=_as_complex(zc),
                 tau=tau)
+
+
+def rlcg(freqs, S_star, Zr, length):
+    """Telegrapher's model: dict(gamma [F] complex, R, L, G, C [F]) from S* [F,2,2] and
+    Z_r [2,F] (complex arrays, as sparams returns them) of a line of `length` metres."""
+    fr, kf = _f64(freqs)
+    F = len(kf)
+    ss = np.ascontiguousarray(np.stack([np.asarray(S_star).real, np.asarray(S_star).imag], axis=-1))
+    zr = np.ascontiguousarray(np.stack([np.asarray(Zr).real, np.asarray(Zr).imag], axis=-1))
+    g = np.zeros((F, 2))
+    out = [np.zeros(F) for _ in range(4)]
+    _check(_lib.yf_rlcg(F, fr, ss.ctypes.data_as(_dp), zr.ctypes.data_as(_dp), float(length),
+                        g.ctypes.data_as(_dp), *[o.ctypes.data_as(_dp) for o in out]))
+    return dict(gamma=g[:, 0] + 1j * g[:, 1], R=out[0], L=out[1], G=out[2], C=out[3])
 
 
 def set_variant(g, variant, tile_y=8, kseg=16):

@@ -62,3 +62,12 @@ def test_paper_microstrip_matches_transmission_line_theory(gpu):
     assert np.max(np.abs(s11[tem] - S[tem, 0, 0])) <= 0.08
     assert np.max(np.abs(s21[tem] - S[tem, 1, 0])) <= 0.08
     assert 0.5 <= np.max(np.abs(S[tem, 0, 0])) <= 0.65
+
+    # Telegrapher's model of the same run (end of Sec. II-A): a lossless line has R and G
+    # negligible against w L and w C, and its L and C are the quasi-static ones
+    rl = gpu.rlcg(f, sp["S_star"], sp["Zr"], l)
+    w = 2 * np.pi * f
+    assert np.all(np.abs(rl["R"][static]) <= 0.05 * w[static] * rl["L"][static])
+    assert np.all(np.abs(rl["G"][static]) <= 0.05 * w[static] * rl["C"][static])
+    assert np.all(np.abs(rl["L"][static] - l_th) <= 0.10 * l_th)
+    assert np.all(np.abs(rl["C"][static] - c_th) <= 0.10 * c_th)
