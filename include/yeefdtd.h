@@ -159,10 +159,22 @@ yf_status yf_set_dft_mode(yf_grid *g, int mask);
  *   2  as 1, with the planes staged by TMA (cp.async.bulk.tensor) three planes ahead of the
  *      computation; a bounded wait that expires makes yf_sync return YF_E_TIMEOUT;
  *   3  as 2, skewed by one plane (H on plane t and E on plane t-1 per iteration, one block
- *      barrier per plane, CPML auxiliaries fetched ahead of the arithmetic).
+ *      barrier per plane, CPML auxiliaries fetched ahead of the arithmetic);
+ *   4  FP32 only: two time steps per pass over the inner box (the nodes at least three cells
+ *      from every absorbing slab, wall, source plane and port plane): one kernel advances it
+ *      from step n to n+2 in a single read of step n, while variant 2's kernels advance the
+ *      rest of the grid one step at a time, with the port epilogue after each step.  Uses a
+ *      third field buffer (6 (nz+1)(ny+1) px words more, px = nx+1 rounded up to 32, allocated here or at the first step and
+ *      freed when another variant is set).  An odd remaining step runs as variant 2.
  * tile_y in {4, 8, 16}, 1 <= kseg <= 64.  All variants compute the same update; results agree to
- * rounding.  Drops captured graphs; may be called between steps. */
+ * rounding.  Drops captured graphs; may be called between steps.  YF_E_INVALID for variant 4
+ * on an FP64 grid or on one with 6 (nz+1)(ny+1) px >= 2^31 (32-bit offsets in its kernel). */
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg);
+
+/* Variant 4's inner box as node ranges x0, x1, y0, y1, z0, z1 (inclusive; all -1 when the
+ * grid has no box, which then steps one step at a time).  Finalises the geometry like a first
+ * yf_step.  YF_E_STATE unless variant 4 is set. */
+yf_status yf_tb_box(yf_grid *g, int box[6]);
 
 /* Autotuner (before the first step): times the TMA-staged fused step (variant 2) for
  * tile_y in {4, 8, 16} x kseg in {8, 16, 32} over `reps` steps each with CUDA events, keeps
@@ -278,6 +290,11 @@ const char *yf_kernel_name(yf_grid *g, int idx);
  * tiling (the stencil launches plus the epilogue), for launch accounting.  Finalises the
  * geometry like a first yf_step would. */
 yf_status yf_launches_per_step(yf_grid *g, int *n);
+
+/* Exact number of kernel launches a yf_step(g, nsteps) issues from the current state (variant
+ * 4 launches per pair of steps; yf_launches_per_step then gives the mean rounded up).
+ * Finalises the geometry like yf_launches_per_step.  YF_E_INVALID for nsteps < 0. */
+yf_status yf_launches(yf_grid *g, long nsteps, long *n);
 
 /* Failure-detection check, no counterpart in the paper: one device thread waits, with the
  * library's bounded-wait rule (a %globaltimer limit, never an unbounded spin), for a flag that

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "yf_internal.h"
@@ -171,7 +172,7 @@ yf_status encode_maps(yf_grid *g)
                                 (cuuint64_t)g->npts * esz};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)(g->tile_y + 2), 1, 3};
     const cuuint32_t one[4] = {1, 1, 1, 1};
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < g->nbuf(); ++b) {
         CUresult r = encode(&g->tmF[b], esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                             4, g->buf[b], gdim, gstr, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -247,7 +248,7 @@ FusedArgs<T> fused_args(const yf_grid *g)
     for (int c = 0; c < 3; ++c) F.cls[c] = g->cls[c];
     F.ctab = (const T *)g->ctab;
     F.A = (const T *)g->buf[g->cur];
-    F.B = (T *)g->buf[g->cur ^ 1];
+    F.B = (T *)g->buf[g->next_buf(g->cur)];
     F.n = g->pml_n;
     F.L = 2 * g->pml_n + 1;
     for (int a = 0; a < 3; ++a) {
@@ -305,6 +306,48 @@ static void build_segments(yf_grid *g)
         const int nyl = d.j1 - d.j0 + 2 * d.m - 1, nzl = d.kt - d.kb + 2 * d.m - 1;
         add(2, p, 2 * (2 * nyl + 2 * nzl));
     }
+}
+
+// variant 4: a third field buffer equal to the current one (nodes no kernel writes must agree
+// in all buffers), maps for it, and the plan
+static yf_status enter_tb(yf_grid *g)
+{
+    if (g->prec != YF_FP32) return fail(YF_E_INVALID, "variant 4 needs FP32 fields");
+    const size_t bytes = 6 * g->npts * g->esz;
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (!g->buf[2]) {
+        YF_CUDA_TRY(cudaMalloc(&g->buf[2], bytes));
+        g->tmap_tile_y = 0;
+    }
+    for (int b = 0; b < 3; ++b)
+        if (b != g->cur) YF_CUDA_TRY(cudaMemcpy(g->buf[b], g->buf[g->cur], bytes, cudaMemcpyDeviceToDevice));
+    yf_status st = encode_maps(g);
+    if (st != YF_OK) return st;
+    return tb_build(g);
+}
+
+// back to two buffers: the current fields move to buf[0] or stay in buf[1]; the auxiliary
+// copies are relabelled so that hpar == cur again (the two-buffer plans assume it)
+static yf_status leave_tb(yf_grid *g)
+{
+    tb_free(g);
+    if (!g->buf[2]) return YF_OK;
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const size_t bytes = 6 * g->npts * g->esz;
+    if (g->cur == 2) {
+        YF_CUDA_TRY(cudaMemcpy(g->buf[0], g->buf[2], bytes, cudaMemcpyDeviceToDevice));
+        g->cur = 0;
+    }
+    YF_CUDA_TRY(cudaMemcpy(g->buf[g->cur ^ 1], g->buf[g->cur], bytes, cudaMemcpyDeviceToDevice));
+    cudaFree(g->buf[2]);
+    g->buf[2] = nullptr;
+    if (g->hpar != g->cur) {
+        for (int a = 0; a < 3; ++a)
+            for (int q = 0; q < 2; ++q) std::swap(g->psiH[0][a][q], g->psiH[1][a][q]);
+        g->hpar = g->cur;
+    }
+    g->tmap_tile_y = 0;
+    return YF_OK;
 }
 
 yf_status finalize(yf_grid *g)
@@ -369,8 +412,11 @@ yf_status finalize(yf_grid *g)
         st = ensure_plan(g);
         if (st != YF_OK) return st;
     }
-    if (g->variant == 2) YF_CUDA_TRY(side_create(&g->side));
-    g->started = true;
+    if (g->variant == 4) {
+        st = enter_tb(g);
+        if (st != YF_OK) return st;
+    }
+    if (g->variant >= 2) YF_CUDA_TRY(side_create(&g->side));
     return YF_OK;
 }
 
@@ -378,7 +424,9 @@ template <typename T>
 static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
 {
     cudaError_t e;
-    if (g->variant >= 1) {
+    if (g->variant == 4) {
+        if ((e = tb_single(g, s)) != cudaSuccess) return e;
+    } else if (g->variant >= 1) {
         if (g->variant == 3)
             e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, s);
         else if (g->variant == 2)
@@ -403,7 +451,7 @@ static cudaError_t launch_one_step(yf_grid *g, cudaStream_t s)
 yf_status reset_state(yf_grid *g)
 {
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (int b = 0; b < 2; ++b) YF_CUDA_TRY(cudaMemsetAsync(g->buf[b], 0, 6 * g->npts * g->esz, g->stream));
+    for (int b = 0; b < g->nbuf(); ++b) YF_CUDA_TRY(cudaMemsetAsync(g->buf[b], 0, 6 * g->npts * g->esz, g->stream));
     for (int a = 0; a < 3; ++a)
         for (int q = 0; q < 2; ++q) {
             void *ps[3] = {g->psiE[a][q], g->psiH[0][a][q], g->psiH[1][a][q]};
@@ -427,19 +475,39 @@ cudaError_t step_direct(yf_grid *g, cudaStream_t s)
     return g->prec == YF_FP32 ? launch_one_step<float>(g, s) : launch_one_step<double>(g, s);
 }
 
+// graph of one chunk from the current state (buffer, auxiliary copy); the state after a
+// chunk equals the state before for variants 1-3 (even chunk) and advances the buffer by
+// chunk mod 3 for variant 4, so graphs are kept per state
+static int graph_key(const yf_grid *g) { return 2 * g->cur + g->hpar; }
+
 static yf_status capture_chunk(yf_grid *g)
 {
     cudaGraph_t graph = nullptr;
+    const int key = graph_key(g), c0 = g->cur, h0 = g->hpar;
     YF_CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int t = 0; t < g->chunk && e == cudaSuccess; ++t) e = step_direct(g, g->stream);
+    if (g->variant == 4)
+        for (int t = 0; t + 1 < g->chunk && e == cudaSuccess; t += 2) e = tb_pair(g, g->stream);
+    else
+        for (int t = 0; t < g->chunk && e == cudaSuccess; ++t) e = step_direct(g, g->stream);
     cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+    // capture only records: the state advances when the graph is launched
+    g->cur = c0;
+    g->hpar = h0;
     if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing step chunk"); }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&g->graph[g->cur], graph, 0);
+    e = cudaGraphInstantiate(&g->graph[key], graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { g->graph[g->cur] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    if (e != cudaSuccess) { g->graph[key] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
     return YF_OK;
+}
+
+// state after one replayed chunk
+static void advance_chunk(yf_grid *g)
+{
+    if (g->variant == 4) {
+        g->cur = (g->cur + g->chunk) % 3;   // chunk is even: hpar unchanged
+    }
 }
 
 }  // namespace yf
@@ -512,9 +580,10 @@ yf_status yf_grid_destroy(yf_grid *g)
 {
     if (!g) return YF_OK;
     if (g->stream) cudaStreamSynchronize(g->stream);
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 6; ++b)
         if (g->graph[b]) cudaGraphExecDestroy(g->graph[b]);
-    for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
+    tb_free(g);
+    for (int b = 0; b < 3; ++b) cudaFree(g->buf[b]);
     cudaFree(g->cls_base);
     for (int a = 0; a < 3; ++a) {
         cudaFree(g->prof[a]);
@@ -695,14 +764,17 @@ yf_status yf_step(yf_grid *g, long n)
     YF_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cs));
     long done = 0;
     if (cs == cudaStreamCaptureStatusNone && n >= g->chunk) {
-        // a chunk has an even number of steps, so the buffer parity is the same before and
-        // after every replay
-        if (!g->graph[g->cur]) {
-            st = capture_chunk(g);
-            if (st != YF_OK) return st;
+        for (; done + g->chunk <= n; done += g->chunk) {
+            if (!g->graph[graph_key(g)]) {
+                st = capture_chunk(g);
+                if (st != YF_OK) return st;
+            }
+            YF_CUDA_TRY(cudaGraphLaunch(g->graph[graph_key(g)], g->stream));
+            advance_chunk(g);
         }
-        for (; done + g->chunk <= n; done += g->chunk) YF_CUDA_TRY(cudaGraphLaunch(g->graph[g->cur], g->stream));
     }
+    if (g->variant == 4)
+        for (; done + 2 <= n; done += 2) YF_CUDA_TRY(tb_pair(g, g->stream));
     for (; done < n; ++done) YF_CUDA_TRY(step_direct(g, g->stream));
     g->steps_done += n;
     return YF_OK;
@@ -767,13 +839,15 @@ yf_status yf_write_fields(yf_grid *g, int comp, const void *src, yf_mem where)
         e = launch_sanitize<double>(fields_of<double>(g, g->cur), g->cls, g->nx, g->ny, g->nz, g->px,
                                     g->plane, g->stream);
     YF_CUDA_TRY(e);
-    // both field buffers carry the written component: the TMA-staged step skips the node
+    // every field buffer carries the written component: the TMA-staged step skips the node
     // column i = nx and row j = ny when they form a tile of their own, and there the two
     // buffers must already agree (only H_x at i = nx and H_y at j = ny live there, and the
     // update leaves them unchanged: their tangential E neighbours are PEC)
     const size_t bytes = (size_t)g->npts * g->esz;
-    YF_CUDA_TRY(cudaMemcpyAsync((char *)g->buf[g->cur ^ 1] + (size_t)comp * bytes, g->fld(comp), bytes,
-                                cudaMemcpyDeviceToDevice, g->stream));
+    for (int b = 0; b < g->nbuf(); ++b)
+        if (b != g->cur)
+            YF_CUDA_TRY(cudaMemcpyAsync((char *)g->buf[b] + (size_t)comp * bytes, g->fld(comp), bytes,
+                                        cudaMemcpyDeviceToDevice, g->stream));
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     return YF_OK;
 }
@@ -882,7 +956,11 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
 {
     cudaError_t e;
     cudaEventRecord(ev[0], g->stream);
-    if (g->variant >= 1) {
+    if (g->variant == 4) {
+        if ((e = tb_single(g, g->stream)) != cudaSuccess) return e;
+        cudaEventRecord(ev[1], g->stream);
+        *nk = 2;
+    } else if (g->variant >= 1) {
         if (g->variant == 3)
             e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream);
         else if (g->variant == 2)
@@ -946,7 +1024,7 @@ const char *yf_kernel_name(yf_grid *g, int idx)
     if (!g) return "";
     if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
     if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
-    if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";
+    if (g->variant == 2 || g->variant == 4) return (idx >= 0 && idx < 2) ? tma[idx] : "";
     return (idx >= 0 && idx < 3) ? ref[idx] : "";
 }
 
@@ -955,6 +1033,10 @@ yf_status yf_launches_per_step(yf_grid *g, int *n)
     if (!g || !n) return fail(YF_E_INVALID, "yf_launches_per_step: NULL argument");
     yf_status st = finalize(g);
     if (st != YF_OK) return st;
+    if (g->variant == 4) {
+        *n = (tb_launches_pair(g) + 1) / 2;
+        return YF_OK;
+    }
     int k = 0;
     if (g->variant == 0) k = 2;
     else if (g->variant == 2)
@@ -964,15 +1046,46 @@ yf_status yf_launches_per_step(yf_grid *g, int *n)
     return YF_OK;
 }
 
+yf_status yf_launches(yf_grid *g, long nsteps, long *n)
+{
+    if (!g || !n || nsteps < 0) return fail(YF_E_INVALID, "yf_launches: bad argument");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    if (g->variant == 4) {
+        *n = (nsteps / 2) * tb_launches_pair(g) + (nsteps % 2) * tb_launches_single(g);
+        return YF_OK;
+    }
+    int k = 0;
+    st = yf_launches_per_step(g, &k);
+    if (st != YF_OK) return st;
+    *n = nsteps * k;
+    return YF_OK;
+}
+
+yf_status yf_tb_box(yf_grid *g, int box[6])
+{
+    if (!g || !box) return fail(YF_E_INVALID, "yf_tb_box: NULL argument");
+    if (g->variant != 4) return fail(YF_E_STATE, "yf_tb_box: variant 4 is not set");
+    yf_status st = finalize(g);
+    if (st != YF_OK) return st;
+    for (int q = 0; q < 6; ++q) box[q] = g->tb->count > 0 ? g->tb->box[q] : -1;
+    return YF_OK;
+}
+
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
 {
     if (!g) return fail(YF_E_INVALID, "yf_set_variant: NULL grid");
-    if (variant < 0 || variant > 3) return fail(YF_E_INVALID, "yf_set_variant: variant must be 0..3");
+    if (variant < 0 || variant > 4) return fail(YF_E_INVALID, "yf_set_variant: variant must be 0..4");
+    if (variant == 4 && g->prec != YF_FP32) return fail(YF_E_INVALID, "yf_set_variant: variant 4 needs FP32 fields");
     if (tile_y != 4 && tile_y != 8 && tile_y != 16) return fail(YF_E_INVALID, "yf_set_variant: tile_y must be 4, 8 or 16");
     if (kseg < 1 || kseg > kMaxKseg) return fail(YF_E_INVALID, "yf_set_variant: kseg must be 1..%d", kMaxKseg);
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 6; ++b)
         if (g->graph[b]) { cudaGraphExecDestroy(g->graph[b]); g->graph[b] = nullptr; }
+    if (g->tb || g->buf[2]) {
+        yf_status st = leave_tb(g);
+        if (st != YF_OK) return st;
+    }
     g->variant = variant;
     g->tile_y = tile_y;
     g->kseg = kseg;
@@ -988,7 +1101,11 @@ yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
         yf_status st = ensure_plan(g);
         if (st != YF_OK) return st;
     }
-    if (g->started && variant == 2) YF_CUDA_TRY(side_create(&g->side));
+    if (g->started && variant == 4) {
+        yf_status st = enter_tb(g);
+        if (st != YF_OK) return st;
+    }
+    if (g->started && variant >= 2) YF_CUDA_TRY(side_create(&g->side));
     return YF_OK;
 }
 
@@ -1070,9 +1187,10 @@ yf_status yf_checkpoint_load(yf_grid *g, const char *path)
     load(g->kahan, (size_t)g->nf_total * 8 * sizeof(float));
     fclose(fp);
     if (!ok) return fail(YF_E_INVALID, "checkpoint %s is truncated", path);
-    // the other field buffer must agree on the nodes a step leaves untouched
-    YF_CUDA_TRY(cudaMemcpy(g->buf[g->cur ^ 1], g->buf[g->cur], 6 * g->npts * g->esz,
-                           cudaMemcpyDeviceToDevice));
+    // the other field buffers must agree on the nodes a step leaves untouched
+    for (int b = 0; b < g->nbuf(); ++b)
+        if (b != g->cur)
+            YF_CUDA_TRY(cudaMemcpy(g->buf[b], g->buf[g->cur], 6 * g->npts * g->esz, cudaMemcpyDeviceToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->ctr, &h.ctr, sizeof(long long), cudaMemcpyHostToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->status, &h.status, sizeof(int), cudaMemcpyHostToDevice));
     g->steps_done = h.steps;

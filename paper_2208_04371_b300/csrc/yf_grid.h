@@ -19,11 +19,14 @@ struct yf_grid {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
 
-    // two field buffers, each ex, ey, ez, hx, hy, hz at stride npts; buf[cur] is current.
-    // The fused step reads buf[cur] and writes buf[cur ^ 1]; the reference kernels update
-    // buf[cur] in place.
-    void *buf[2] = {};
+    // field buffers, each ex, ey, ez, hx, hy, hz at stride npts; buf[cur] is current.
+    // The fused step reads buf[cur] and writes the next buffer (buf[cur ^ 1]; variant 4
+    // rotates three: buf[(cur + 1) % 3]); the reference kernels update buf[cur] in place.
+    // buf[2] exists only while variant 4 is set.
+    void *buf[3] = {};
     int cur = 0;
+    int next_buf(int b) const { return buf[2] ? (b + 1) % 3 : b ^ 1; }
+    int nbuf() const { return buf[2] ? 3 : 2; }
     void *fld(int c) const { return (char *)buf[cur] + (size_t)c * npts * esz; }
     uint8_t *cls[3] = {};         // per-edge material class of ex, ey, ez (0 = PEC)
     void *ctab = nullptr;         // [256][2] (Ca, Cb) in field precision
@@ -72,9 +75,10 @@ struct yf_grid {
 
     bool started = false;
     bool geometry_open = false;   // after yf_reset: materials and sheets may change
-    int variant = 2;              // 0: reference H and E, 1: fused step, 2: fused + TMA
+    int variant = 2;              // 0: reference H and E, 1: fused step, 2: fused + TMA,
+                                  // 3: skewed, 4: two-step inner box (FP32)
     uint8_t *cls_base = nullptr;  // the three class arrays, contiguous
-    CUtensorMap tmF[2];           // field buffers as 4-D tensors (variant 2)
+    CUtensorMap tmF[3];           // field buffers as 4-D tensors (variants 2 to 4)
     CUtensorMap tmC;              // edge classes as a 4-D tensor
     int tmap_tile_y = 0;          // tile the maps were encoded for (0: not encoded)
     yf::SideStream side = {};     // CPML work of variant 2 overlaps the interior
@@ -83,7 +87,8 @@ struct yf_grid {
     int tile_y = 8;               // fused: block rows (block is 32 x tile_y)
     int kseg = 16;                // fused: z-planes per block
     int chunk = 32;               // steps per captured graph (even)
-    cudaGraphExec_t graph[2] = {};   // one per starting buffer parity
+    cudaGraphExec_t graph[6] = {};   // one per starting state cur * 2 + hpar
+    yf::TbPlan *tb = nullptr;        // variant 4
 };
 
 namespace yf {
@@ -100,6 +105,14 @@ std::string tune_key(const char *kind, yf_prec prec, long cells, int pml);
 template <typename T>
 yf_status build_plan(const std::vector<yf_grid *> &grids, int tile_y, int kseg, TmaPlan *pl);
 void free_plan(TmaPlan *pl);
+// variant 4 (yf_tb.cu): plan (box, work items, arguments, maps) for the current buffers;
+// one time step over the whole grid; two time steps (box + frame); teardown
+yf_status tb_build(yf_grid *g);
+void tb_free(yf_grid *g);
+cudaError_t tb_single(yf_grid *g, cudaStream_t s);
+cudaError_t tb_pair(yf_grid *g, cudaStream_t s);
+int tb_launches_pair(const yf_grid *g);
+int tb_launches_single(const yf_grid *g);
 template <typename T>
 Fields<T> fields_of(const yf_grid *g, int b);
 template <typename T>

@@ -180,6 +180,32 @@ cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *stat
                             const SideStream *side);
 void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
                const int hi[3], std::vector<BatchItem> items[5]);
+// two-step update of the inner box (yf_tb.cu, FP32): A = the buffer at step n (read through
+// the tensor maps), C receives E^{n+2}, H^{n+3/2} on the box, B the box's outer node layer at
+// E^{n+1}, H^{n+1/2}.  The box [bx0, bx1] x [by0, by1] x [bz0, bz1] is a union of 32 x 8 tiles.
+struct TbArgs {
+    int px;
+    long plane, npts;
+    float rdx, rdy, rdz, db;
+    const float *ctab;
+    float *B, *C;
+    int bx0, bx1, by0, by1, bz0, bz1;
+};
+// plan of variant 4 for one grid
+struct TbPlan {
+    TmaPlan full;        // single step over the grid; arguments and maps by slot 2 * src + hpar
+    TmaPlan frame;       // single step outside the box; shares full's arguments and maps
+    BatchItem *items;    // two-step items of the box
+    int count;
+    TbArgs *args;        // [3] by source buffer
+    CUtensorMap *maps;   // [3][window map, class map]
+    int box[6];          // bx0, bx1, by0, by1, bz0, bz1
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+cudaError_t tb_prepare();
+cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,
+                       int phase, int *status, cudaStream_t s);
 // skewed TMA-staged fused step (yf_skew.cu), same tensor maps as launch_tma
 cudaError_t skew_prepare();
 template <typename T>

@@ -1,0 +1,601 @@
+// Two-step (temporally blocked) Yee update of the inner box, FP32 (variant 4).
+//
+// The inner box is a set of whole 32 x 8 tiles and a z range that stay at least two nodes
+// away from every CPML slab, domain wall, source plane and port plane, so only the plain
+// Yee update (materials through the class table) happens in and around it.  One block takes
+// one tile over a z segment [kb, ke] and advances it from step n (buffer A) to step n + 2
+// (buffer C) in one pass over HBM:
+//   S1  H^{n+1/2}  on the tile grown by 2 nodes on the low sides, 1 on the high sides
+//   S2  E^{n+1}    on the tile grown by 1 node on every side
+//   S3  H^{n+3/2}  on the tile grown by 1 node on the low sides
+//   S4  E^{n+2}    on the tile, written to C together with H^{n+3/2}
+// (the far corner of the S1 and S2 regions feeds nothing and is skipped).  The grown rings
+// recompute what neighbouring blocks (or the single-step frame) own, from the same step-n data.
+// z is marched with the stages skewed so that each plane iteration q has two phases separated
+// by one block barrier: {S1 on plane q-1, S3 on plane q-3}, then {S2 on plane q-1, S4 on plane
+// q-3}; every input of a phase comes from an earlier phase.  Step-n planes arrive by TMA two planes ahead: E and H windows of
+// 40 x 12 nodes (x from i0-4, y from j0-2) in four stages, the class tiles (64 x 10) in six
+// slots (S4 reads the classes of plane q-3); H^{n+1/2} and E^{n+1} are kept for three planes,
+// H^{n+3/2} for two.
+//
+// The single-step frame advances the rest of the grid n -> n+1 (A -> B) and n+1 -> n+2
+// (B -> C).  Its second step reads the box's outermost node layer at n + 1 from B (a window
+// reaches one node into the box), so this kernel also writes E^{n+1} and H^{n+1/2} of that
+// layer into B.  Every mbarrier wait is bounded; a wait that gives up sets bit 1 of the status
+// word and the block returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "yf_grid.h"
+#include "yf_internal.h"
+
+namespace yf {
+namespace {
+
+constexpr int TBX = 32, TBY = 8;                     // output tile
+constexpr int NWARP = 12, TBN = 32 * NWARP;          // block
+constexpr int WXN = 40, WYN = 12, WN = WXN * WYN;    // windows: x from i0-4, y from j0-2
+constexpr int CXN = 64, CYN = 10, CN = CXN * CYN;    // class tile: x from i0-16, y from j0-1
+constexpr int FST = 4, CSL = 6;                      // field stages, class slots
+constexpr int PL = 3 * WN * 4;                       // one plane of three components (bytes)
+constexpr int C_OFF = FST * 2 * PL;                  // stage s: E at s * 2PL, H at s * 2PL + PL
+constexpr int HA_OFF = C_OFF + CSL * 3 * CN;         // H^{n+1/2} [3][3][WN]
+constexpr int EA_OFF = HA_OFF + 3 * PL;              // E^{n+1}   [3][3][WN]
+constexpr int HB_OFF = EA_OFF + 3 * PL;              // H^{n+3/2} [2][3][WN]
+constexpr int CT_OFF = HB_OFF + 2 * PL;              // (Ca, Cb) per class
+constexpr int BAR_OFF = CT_OFF + 2 * kMaxClasses * 4;
+constexpr int TB_BYTES = BAR_OFF + 8 * FST;
+constexpr uint32_t TX_BYTES = 2 * PL + 3 * CN;
+static_assert(PL % 128 == 0 && C_OFF % 128 == 0 && (3 * CN) % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(2 * (TB_BYTES + 1024) <= 228 * 1024, "two blocks per SM");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 26); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int c,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(bar)
+        : "memory");
+}
+
+// Each thread updates one pair of x-adjacent nodes (i, i+1), i - i0 even, per phase.  A
+// half-warp takes the first 16 pairs of one row (128 contiguous bytes, no bank conflicts);
+// the one or two pairs left at the right end of each row form short strips:
+//   phase 1: threads   0..175 S1 rows j0-2..j0+8, pairs 0..15 from i0-2;  176..197 pairs 16, 17
+//            threads 224..367 S3 rows j0-1..j0+7, pairs 0..15 from i0-2;  368..376 pair 16
+//   phase 2: threads   0..159 S2 rows j0-1..j0+8, pairs 0..15 from i0-2;  160..179 pairs 16, 17
+//            threads 192..319 S4 rows j0..j0+7,   pairs 0..15 from i0
+// so every warp runs one stage.  Pairs reach one node past the needed ranges on the left of
+// S2 and S3 and on the right of S1 and S2; those extra nodes read neighbours nobody computed
+// and feed nothing.  The pair's values move as float2 (64-bit shared loads, one 32-bit load
+// for the neighbour shifted by one node in x) through Blackwell's paired FP32 arithmetic.
+// w, c: window and class-tile index of the pair's first node; g: its offset j px + i in a
+// field plane; own: the pair is in the block's tile; lay: a node of it lies on the box's
+// outer layer in x or y.
+struct Task {
+    int kind, w, c, g;
+    bool own, lay;
+};
+
+// pair (row, index) of element e of a stage with R rows and `extra` strip pairs per row
+__device__ __forceinline__ bool stage_pair(int e, int R, int extra, int *row, int *pair)
+{
+    if (e < 16 * R) { *row = e >> 4; *pair = e & 15; return true; }
+    e -= 16 * R;
+    if (e >= extra * R) return false;
+    *row = extra == 2 ? e >> 1 : e;
+    *pair = 16 + (extra == 2 ? (e & 1) : 0);
+    return true;
+}
+
+__device__ __forceinline__ Task make_task(int phase, int tid, int i0, int j0, const TbArgs &P)
+{
+    Task k{0, 0, 0, 0, false, false};
+    int i = 0, j = 0, r, q;
+    if (phase == 1) {
+        if (tid < 224 && stage_pair(tid, 11, 2, &r, &q)) { k.kind = 1; i = i0 - 2 + 2 * q; j = j0 - 2 + r; }
+        else if (tid >= 224 && stage_pair(tid - 224, 9, 1, &r, &q)) { k.kind = 3; i = i0 - 2 + 2 * q; j = j0 - 1 + r; }
+    } else {
+        if (tid < 192 && stage_pair(tid, 10, 2, &r, &q)) { k.kind = 2; i = i0 - 2 + 2 * q; j = j0 - 1 + r; }
+        else if (tid >= 192 && stage_pair(tid - 192, 8, 0, &r, &q)) { k.kind = 4; i = i0 + 2 * q; j = j0 + r; }
+    }
+    if (!k.kind) return k;
+    k.w = (j - j0 + 2) * WXN + (i - i0 + 4);
+    k.c = (j - j0 + 1) * CXN + (i - i0 + 16);
+    k.g = j * P.px + i;
+    k.own = i >= i0 && i + 1 < i0 + TBX && j >= j0 && j < j0 + TBY;
+    k.lay = i == P.bx0 || i + 1 == P.bx1 || j == P.by0 || j == P.by1;
+    return k;
+}
+
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+// a - b, exactly rounded (fused multiply-add by -1 rounds once)
+__device__ __forceinline__ float2 dif(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// d1 r1 - d2 r2, with nr2 = -r2 (one rounding for the product d1 r1, one for the fused tail)
+__device__ __forceinline__ float2 curl(float2 d1, float2 r1, float2 d2, float2 nr2)
+{
+    return __ffma2_rn(d2, nr2, __fmul2_rn(d1, r1));
+}
+
+struct Coef {
+    float2 rx, ry, rz, nrx, nry, nrz, ndb;
+};
+
+// H update of a node pair (S1 from step-n data, S3 from E^{n+1}): e0/e1 = E on planes p, p+1,
+// h0 = H on plane p, all in window layout; result into hw
+__device__ __forceinline__ void h_pair(const float *e0, const float *e1, const float *h0, float *hw, int w,
+                                       const Coef &K)
+{
+    const float2 ex = ld2(e0 + w), ey = ld2(e0 + WN + w), ez = ld2(e0 + 2 * WN + w);
+    const float2 exU = ld2(e0 + w + WXN), ezU = ld2(e0 + 2 * WN + w + WXN);
+    const float2 eyR = make_float2(ey.y, e0[WN + w + 2]), ezR = make_float2(ez.y, e0[2 * WN + w + 2]);
+    const float2 ex1 = ld2(e1 + w), ey1 = ld2(e1 + WN + w);
+    // H_x -= dt/mu0 (dEz/dy - dEy/dz), H_y -= dt/mu0 (dEx/dz - dEz/dx), H_z -= dt/mu0 (dEy/dx - dEx/dy)
+    st2(hw + w, __ffma2_rn(curl(dif(ezU, ez), K.ry, dif(ey1, ey), K.nrz), K.ndb, ld2(h0 + w)));
+    st2(hw + WN + w, __ffma2_rn(curl(dif(ex1, ex), K.rz, dif(ezR, ez), K.nrx), K.ndb, ld2(h0 + WN + w)));
+    st2(hw + 2 * WN + w, __ffma2_rn(curl(dif(eyR, ey), K.rx, dif(exU, ex), K.nry), K.ndb, ld2(h0 + 2 * WN + w)));
+}
+
+// E update of a node pair: eo = E before, ha/hp = H on planes k, k-1, cl = class tile of
+// plane k.  Class 0 (PEC) has Ca = Cb = 0, so its edges stay zero.
+__device__ __forceinline__ void e_pair(const float *eo, const float *ha, const float *hp, const unsigned char *cl,
+                                       const float2 *CT, int w, int c, const Coef &K, float2 *vx, float2 *vy,
+                                       float2 *vz)
+{
+    const float2 hx = ld2(ha + w), hy = ld2(ha + WN + w), hz = ld2(ha + 2 * WN + w);
+    const float2 hxD = ld2(ha + w - WXN), hzD = ld2(ha + 2 * WN + w - WXN);
+    const float2 hyL = make_float2(ha[WN + w - 1], hy.x), hzL = make_float2(ha[2 * WN + w - 1], hz.x);
+    const float2 hpx = ld2(hp + w), hpy = ld2(hp + WN + w);
+    const unsigned cxx = *reinterpret_cast<const unsigned short *>(cl + c);
+    const unsigned cyy = *reinterpret_cast<const unsigned short *>(cl + CN + c);
+    const unsigned czz = *reinterpret_cast<const unsigned short *>(cl + 2 * CN + c);
+    const float2 ax0 = CT[cxx & 255], ax1 = CT[cxx >> 8];
+    const float2 ay0 = CT[cyy & 255], ay1 = CT[cyy >> 8];
+    const float2 az0 = CT[czz & 255], az1 = CT[czz >> 8];
+    // E_x = Ca E_x + Cb (dHz/dy - dHy/dz), E_y = Ca E_y + Cb (dHx/dz - dHz/dx),
+    // E_z = Ca E_z + Cb (dHy/dx - dHx/dy)
+    *vx = __ffma2_rn(make_float2(ax0.y, ax1.y), curl(dif(hz, hzD), K.ry, dif(hy, hpy), K.nrz),
+                     __fmul2_rn(make_float2(ax0.x, ax1.x), ld2(eo + w)));
+    *vy = __ffma2_rn(make_float2(ay0.y, ay1.y), curl(dif(hx, hpx), K.rz, dif(hz, hzL), K.nrx),
+                     __fmul2_rn(make_float2(ay0.x, ay1.x), ld2(eo + WN + w)));
+    *vz = __ffma2_rn(make_float2(az0.y, az1.y), curl(dif(hy, hyL), K.rx, dif(hx, hxD), K.nry),
+                     __fmul2_rn(make_float2(az0.x, az1.x), ld2(eo + 2 * WN + w)));
+}
+
+__global__ void __launch_bounds__(TBN, 2)
+k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, int phase_buf, int *status)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const BatchItem it = items[blockIdx.x];
+    const TbArgs P = args[phase_buf];
+    const CUtensorMap *tmW = maps + 2 * phase_buf, *tmC = maps + 2 * phase_buf + 1;
+    const int tid = threadIdx.x;
+    const int i0 = it.i0, j0 = it.j0, kb = it.kb, ke = it.ke;
+    float2 *CT = reinterpret_cast<float2 *>(sm + CT_OFF);
+    const uint32_t bar0 = smem_u32(sm + BAR_OFF);
+    if (smem_u32(sm) & 127u) {
+        if (tid == 0) atomicOr(status, 4);
+        return;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < FST; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int q = tid; q < kMaxClasses; q += TBN) CT[q] = make_float2(P.ctab[2 * q], P.ctab[2 * q + 1]);
+    __syncthreads();
+
+    auto issue = [&](int p) {   // thread 0: step-n plane p -> field stage p & 3, class slot p % 6
+        unsigned char *st = sm + (p & 3) * 2 * PL;
+        const uint32_t bar = bar0 + 8 * (p & 3);
+        mbar_expect_tx(bar, TX_BYTES);
+        tma_load_4d(smem_u32(st), tmW, i0 - 4, j0 - 2, p, 0, bar);
+        tma_load_4d(smem_u32(st + PL), tmW, i0 - 4, j0 - 2, p, 3, bar);
+        tma_load_4d(smem_u32(sm + C_OFF + (p % CSL) * 3 * CN), tmC, i0 - 16, j0 - 1, p, 0, bar);
+    };
+    uint32_t ph = 0;   // thread 0: parity of each stage's next completion
+    auto wait_plane = [&](int p) -> bool {
+        bool ok = true;
+        if (tid == 0) {
+            const int s = p & 3;
+            ok = mbar_wait(bar0 + 8 * s, (ph >> s) & 1u);
+            ph ^= 1u << s;
+        }
+        return __syncthreads_and(ok);
+    };
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(kb - 2);
+        issue(kb - 1);
+        issue(kb);
+    }
+    const Task T1 = make_task(1, tid, i0, j0, P), T2 = make_task(2, tid, i0, j0, P);
+    if (!wait_plane(kb - 2)) {
+        if (tid == 0) atomicOr(status, 2);
+        return;
+    }
+
+    Coef K;
+    K.rx = make_float2(P.rdx, P.rdx);
+    K.ry = make_float2(P.rdy, P.rdy);
+    K.rz = make_float2(P.rdz, P.rdz);
+    K.nrx = make_float2(-P.rdx, -P.rdx);
+    K.nry = make_float2(-P.rdy, -P.rdy);
+    K.nrz = make_float2(-P.rdz, -P.rdz);
+    K.ndb = make_float2(-P.db, -P.db);
+    const int plane = (int)P.plane, npts = (int)P.npts;
+    float *const HA = reinterpret_cast<float *>(sm + HA_OFF);
+    float *const EA = reinterpret_cast<float *>(sm + EA_OFF);
+    float *const HB = reinterpret_cast<float *>(sm + HB_OFF);
+    const bool xy_edge = i0 == P.bx0 || i0 + TBX - 1 == P.bx1 || j0 == P.by0 || j0 + TBY - 1 == P.by1;
+    // ring slots of plane q-1: a = (q-1) mod 3 (H^{n+1/2}, E^{n+1}), b = (q-1) mod 6 (classes)
+    int a = (kb - 2) % 3, b = (kb - 2) % CSL;
+
+    for (int q = kb - 1; q <= ke + 3; ++q) {
+        if (q <= ke + 2) {
+            if (!wait_plane(q)) {
+                if (tid == 0) atomicOr(status, 2);
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
+        // every thread has finished plane q-2's stage and plane q-4's classes: refill them
+        if (tid == 0 && q <= ke) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(q + 2);
+        }
+        const int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;   // (q-3) mod 3, (q-2) mod 3
+        const int p3 = q - 3;
+        const float *f0 = reinterpret_cast<const float *>(sm + ((q - 1) & 3) * 2 * PL);   // step n, plane q-1
+        const float *f1 = reinterpret_cast<const float *>(sm + (q & 3) * 2 * PL);         // step n, plane q
+        float *haw = HA + a * 3 * WN;                 // H^{n+1/2} plane q-1
+        const float *hap = HA + a2 * 3 * WN;          // plane q-2
+        const float *ha3 = HA + a1 * 3 * WN;          // plane q-3
+        float *eaw = EA + a * 3 * WN;                 // E^{n+1} plane q-1
+        const float *ea3 = EA + a1 * 3 * WN, *ea2 = EA + a2 * 3 * WN;
+        float *hb3 = HB + (p3 & 1) * 3 * WN;          // H^{n+3/2} plane q-3
+        const float *hb4 = HB + ((p3 + 1) & 1) * 3 * WN;
+        const unsigned char *cl1 = sm + C_OFF + b * 3 * CN;
+        const unsigned char *cl3 = sm + C_OFF + (b >= 2 ? b - 2 : b + 4) * 3 * CN;
+
+        // phase 1: S1 on plane q-1, S3 on plane q-3
+        if (T1.kind == 1 && q <= ke + 2) h_pair(f0, f1, f0 + 3 * WN, haw, T1.w, K);
+        if (T1.kind == 3 && q >= kb + 2) h_pair(ea3, ea2, ha3, hb3, T1.w, K);
+        __syncthreads();
+        // phase 2: S2 on plane q-1, S4 on plane q-3 (into C)
+        if (T2.kind == 2 && q >= kb && q <= ke + 2) {
+            float2 vx, vy, vz;
+            e_pair(f0, haw, hap, cl1, CT, T2.w, T2.c, K, &vx, &vy, &vz);
+            st2(eaw + T2.w, vx);
+            st2(eaw + WN + T2.w, vy);
+            st2(eaw + 2 * WN + T2.w, vz);
+            // the box's outer node layer at n + 1 (and its H^{n+1/2}) for the frame's second
+            // step; a pair with one layer node writes both (the other value is also correct)
+            const int k = q - 1;
+            if (T2.own && k >= kb && k <= ke && (k == P.bz0 || k == P.bz1 || (xy_edge && T2.lay))) {
+                float *B = P.B + (k * plane + T2.g);
+                st2(B, vx);
+                st2(B + npts, vy);
+                st2(B + 2 * npts, vz);
+                st2(B + 3 * npts, ld2(haw + T2.w));
+                st2(B + 4 * npts, ld2(haw + WN + T2.w));
+                st2(B + 5 * npts, ld2(haw + 2 * WN + T2.w));
+            }
+        }
+        if (T2.kind == 4 && q >= kb + 3) {
+            float2 vx, vy, vz;
+            e_pair(ea3, hb3, hb4, cl3, CT, T2.w, T2.c, K, &vx, &vy, &vz);
+            float *C = P.C + (p3 * plane + T2.g);
+            st2(C, vx);
+            st2(C + npts, vy);
+            st2(C + 2 * npts, vz);
+            st2(C + 3 * npts, ld2(hb3 + T2.w));
+            st2(C + 4 * npts, ld2(hb3 + WN + T2.w));
+            st2(C + 5 * npts, ld2(hb3 + 2 * WN + T2.w));
+        }
+        a = a == 2 ? 0 : a + 1;
+        b = b == CSL - 1 ? 0 : b + 1;
+    }
+}
+
+constexpr int kTbSeg = 32;   // z-planes per two-step block
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// The box.  A two-step block over tile (i0, j0) and planes kb..ke reads step-n nodes
+// i in [i0-2, i0+33], j in [j0-2, j0+9], k in [kb-2, ke+2] and recomputes H and E on most of
+// them; all of these must see the plain update only.  So the box keeps three nodes from every
+// absorbing slab and domain wall on the low sides and two (x, y) or three (z) on the high
+// sides, and tiles whose x range widened by four nodes holds the source plane or a port plane
+// are left out (the port epilogue reads and the source writes the frame's fields between
+// the two steps).  x: the longest run of admissible 32-node tile columns; y: rows aligned to
+// the frame's tile height; z: every admissible plane.  Returns false when no box fits.
+bool choose_box(const yf_grid *g, int box[6])
+{
+    const int n = g->pml_n;
+    const int XL = g->pml_lo[0] ? n : 0, XH = g->pml_hi[0] ? g->nx - n : g->nx;
+    const int YL = g->pml_lo[1] ? n : 0, YH = g->pml_hi[1] ? g->ny - n : g->ny;
+    const int ZL = g->pml_lo[2] ? n : 0, ZH = g->pml_hi[2] ? g->nz - n : g->nz;
+    std::vector<int> special;
+    if (g->has_src) special.push_back(g->src_plane);
+    for (const PortDev &d : g->ports) special.push_back(d.plane);
+    const int ntx = g->nx / 32;
+    int best = 0, bt0 = 0, run = 0;
+    for (int tx = 0; tx < ntx; ++tx) {
+        const int i0 = 32 * tx;
+        bool ok = i0 - 3 >= XL && i0 + 34 <= XH;
+        for (int s : special) ok = ok && !(s >= i0 - 4 && s <= i0 + 35);
+        run = ok ? run + 1 : 0;
+        if (run > best) { best = run; bt0 = tx - run + 1; }
+    }
+    const int A = std::max(8, g->tile_y);
+    const int by0 = (YL + 3 + A - 1) / A * A, byE = (YH - 2) / A * A;
+    const int bz0 = ZL + 3, bz1 = ZH - 3;
+    if (best < 1 || byE <= by0 || bz1 - bz0 + 1 < 4) return false;
+    box[0] = 32 * bt0;
+    box[1] = 32 * (bt0 + best) - 1;
+    box[2] = by0;
+    box[3] = byE - 1;
+    box[4] = bz0;
+    box[5] = bz1;
+    return true;
+}
+
+yf_status upload_items(const std::vector<BatchItem> items[5], TmaPlan *pl)
+{
+    std::vector<BatchItem> all;
+    for (int k = 0; k < 5; ++k) {
+        pl->offset[k] = (int)all.size();
+        pl->count[k] = (int)items[k].size();
+        all.insert(all.end(), items[k].begin(), items[k].end());
+    }
+    YF_CUDA_TRY(cudaMalloc(&pl->items, std::max<size_t>(1, all.size()) * sizeof(BatchItem)));
+    if (!all.empty())
+        YF_CUDA_TRY(cudaMemcpy(pl->items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    return YF_OK;
+}
+
+int kinds_used(const TmaPlan &pl)
+{
+    int k = 0;
+    for (int q = 0; q < 5; ++q) k += pl.count[q] > 0;
+    return k;
+}
+
+}  // namespace
+
+cudaError_t tb_prepare()
+{
+    return cudaFuncSetAttribute(k_yee_tb2, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_BYTES);
+}
+
+cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,
+                       int phase, int *status, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_yee_tb2<<<count, TBN, TB_BYTES, s>>>(items, args, maps, phase, status);
+    return cudaGetLastError();
+}
+
+void tb_free(yf_grid *g)
+{
+    TbPlan *t = g->tb;
+    if (!t) return;
+    if (t->stream) cudaStreamSynchronize(t->stream);
+    cudaFree(t->full.items);
+    cudaFree(t->full.args);
+    cudaFree(t->full.maps);
+    cudaFree(t->frame.items);
+    cudaFree(t->items);
+    cudaFree(t->args);
+    cudaFree(t->maps);
+    if (t->fork) cudaEventDestroy(t->fork);
+    if (t->join) cudaEventDestroy(t->join);
+    if (t->stream) cudaStreamDestroy(t->stream);
+    delete t;
+    g->tb = nullptr;
+}
+
+// Plan of variant 4 on a finalised FP32 grid whose three field buffers exist and whose field
+// maps (tmF[0..2], tmC) are encoded for the grid's tile height.
+yf_status tb_build(yf_grid *g)
+{
+    if (g->tb) return YF_OK;
+    if (g->prec != YF_FP32) return fail(YF_E_INVALID, "variant 4 needs FP32 fields");
+    if (!g->buf[2]) return fail(YF_E_STATE, "variant 4: third field buffer missing");
+    // the two-step kernel indexes a buffer's six components with 32-bit offsets
+    if (6 * g->npts > 2147483647L)
+        return fail(YF_E_INVALID, "variant 4 needs 6 (nz+1)(ny+1) px < 2^31 (grid has %ld points)", g->npts);
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
+    if (!encode) return fail(YF_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    TbPlan *t = new TbPlan();
+    g->tb = t;
+    auto bail = [&](yf_status st) { tb_free(g); return st; };
+
+    std::vector<BatchItem> full[5], frame[5], two;
+    tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full);
+    const bool have_box = choose_box(g, t->box);
+    const int *B = t->box;
+    for (int k = 0; k < 5; ++k)
+        for (const BatchItem &it : full[k]) {
+            const bool inxy = have_box && it.i0 >= B[0] && it.i0 <= B[1] && it.j0 >= B[2] && it.j0 <= B[3];
+            if (!inxy || it.ke < B[4] || it.kb > B[5]) {
+                frame[k].push_back(it);
+                continue;
+            }
+            if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
+            if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
+        }
+    if (have_box)
+        for (int kb = B[4]; kb <= B[5]; kb += kTbSeg)
+            for (int j0 = B[2]; j0 <= B[3]; j0 += TBY)
+                for (int i0 = B[0]; i0 <= B[1]; i0 += TBX)
+                    two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + kTbSeg - 1)});
+    yf_status st;
+    if ((st = upload_items(full, &t->full)) != YF_OK) return bail(st);
+    if ((st = upload_items(frame, &t->frame)) != YF_OK) return bail(st);
+    t->count = (int)two.size();
+    if (cudaMalloc(&t->items, std::max<size_t>(1, two.size()) * sizeof(BatchItem)) != cudaSuccess ||
+        (!two.empty() && cudaMemcpy(t->items, two.data(), two.size() * sizeof(BatchItem),
+                                    cudaMemcpyHostToDevice) != cudaSuccess))
+        return bail(fail(YF_E_OOM, "variant 4: work items"));
+
+    // single-step arguments by slot 2 * src + hpar (B = the next buffer), shared by both plans
+    std::vector<FusedArgs<float>> fa(6);
+    std::vector<CUtensorMap> fm(12);
+    const int c0 = g->cur, h0 = g->hpar;
+    for (int r = 0; r < 3; ++r)
+        for (int h = 0; h < 2; ++h) {
+            g->cur = r;
+            g->hpar = h;
+            fa[2 * r + h] = fused_args<float>(g);
+            fm[2 * (2 * r + h)] = g->tmF[r];
+            fm[2 * (2 * r + h) + 1] = g->tmC;
+        }
+    g->cur = c0;
+    g->hpar = h0;
+    if (cudaMalloc(&t->full.args, fa.size() * sizeof(FusedArgs<float>)) != cudaSuccess ||
+        cudaMemcpy(t->full.args, fa.data(), fa.size() * sizeof(FusedArgs<float>), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&t->full.maps, fm.size() * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMemcpy(t->full.maps, fm.data(), fm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(YF_E_OOM, "variant 4: step arguments"));
+    t->frame.args = t->full.args;
+    t->frame.maps = t->full.maps;
+
+    // two-step arguments and maps by source buffer r: B = buf[r+1], C = buf[r+2]
+    TbArgs ta[3];
+    CUtensorMap tm[6];
+    const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
+    const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
+    const cuuint32_t wbox[4] = {WXN, WYN, 1, 3};
+    const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
+    const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
+    const cuuint32_t cbox[4] = {CXN, CYN, 1, 3};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    for (int r = 0; r < 3; ++r) {
+        TbArgs &a = ta[r];
+        a.px = g->px;
+        a.plane = g->plane;
+        a.npts = g->npts;
+        a.rdx = (float)(1.0 / g->dx);
+        a.rdy = (float)(1.0 / g->dy);
+        a.rdz = (float)(1.0 / g->dz);
+        a.db = (float)(g->dt / kMu0);
+        a.ctab = (const float *)g->ctab;
+        a.B = (float *)g->buf[(r + 1) % 3];
+        a.C = (float *)g->buf[(r + 2) % 3];
+        a.bx0 = B[0]; a.bx1 = B[1]; a.by0 = B[2]; a.by1 = B[3]; a.bz0 = B[4]; a.bz1 = B[5];
+        CUresult cr = encode(&tm[2 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr == CUDA_SUCCESS)
+            cr = encode(&tm[2 * r + 1], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return bail(fail(YF_E_CUDA, "variant 4: tensor map encoding failed (%d)", (int)cr));
+    }
+    if (cudaMalloc(&t->args, sizeof(ta)) != cudaSuccess ||
+        cudaMemcpy(t->args, ta, sizeof(ta), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&t->maps, sizeof(tm)) != cudaSuccess ||
+        cudaMemcpy(t->maps, tm, sizeof(tm), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(YF_E_OOM, "variant 4: two-step arguments"));
+    if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(YF_E_CUDA, "variant 4: stream set-up"));
+    cudaError_t e = tb_prepare();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "variant 4: shared-memory opt-in"));
+    return YF_OK;
+}
+
+// one time step over the whole grid (stencil only; the caller adds the epilogue)
+cudaError_t tb_single(yf_grid *g, cudaStream_t s)
+{
+    TbPlan &t = *g->tb;
+    cudaError_t e = launch_tma_plan<float>(t.full, g->tile_y, 2 * g->cur + g->hpar, g->status, s, &g->side);
+    if (e != cudaSuccess) return e;
+    g->cur = (g->cur + 1) % 3;
+    g->hpar ^= 1;
+    return cudaSuccess;
+}
+
+// two time steps with both epilogues: the box n -> n+2 on a side stream, concurrently the
+// frame n -> n+1 and its epilogue; then, once the box is done, the frame n+1 -> n+2 and its
+// epilogue
+cudaError_t tb_pair(yf_grid *g, cudaStream_t s)
+{
+    TbPlan &t = *g->tb;
+    const int r = g->cur, h = g->hpar, r1 = (r + 1) % 3;
+    cudaError_t e;
+    const bool box = t.count > 0;
+    if (box) {
+        if ((e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(t.stream, t.fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(t.join, t.stream)) != cudaSuccess) return e;
+    }
+    if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r + h, g->status, s, &g->side)) != cudaSuccess) return e;
+    g->cur = r1;
+    g->hpar = h ^ 1;
+    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
+    if (box && (e = cudaStreamWaitEvent(s, t.join, 0)) != cudaSuccess) return e;
+    if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r1 + (h ^ 1), g->status, s, &g->side)) != cudaSuccess)
+        return e;
+    g->cur = (r + 2) % 3;
+    g->hpar = h;
+    return launch_epilogue<float>(epi_params<float>(g), s);
+}
+
+int tb_launches_pair(const yf_grid *g)
+{
+    return 2 * kinds_used(g->tb->frame) + (g->tb->count > 0) + 2;
+}
+
+int tb_launches_single(const yf_grid *g) { return kinds_used(g->tb->full) + 1; }
+
+}  // namespace yf

@@ -101,6 +101,8 @@ _SIGS = {
     "yf_read_sparams": (_i, [_vp, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_read_sparams_acc": (_i, [_vp, _i, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_launches_per_step": (_i, [_vp, C.POINTER(_i)]),
+    "yf_launches": (_i, [_vp, C.c_long, C.POINTER(C.c_long)]),
+    "yf_tb_box": (_i, [_vp, C.POINTER(_i)]),
     "yf_bounded_wait_check": (_i, [_i, _d]),
     "yf_rlcg": (_i, [_i, _dp, _dp, _dp, _d, _dp, _dp, _dp, _dp, _dp]),
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -397,6 +399,20 @@ def bounded_wait_check(preset_flag: bool, limit_seconds: float):
 def launches_per_step(g) -> int:
     n = C.c_int()
     _check(_lib.yf_launches_per_step(C.c_void_p(g), C.byref(n)))
+    return n.value
+
+
+def tb_box(g):
+    """Variant 4's inner box (x0, x1, y0, y1, z0, z1), or None when the grid has none."""
+    b = (_i * 6)()
+    _check(_lib.yf_tb_box(C.c_void_p(g), b))
+    return None if b[0] < 0 else tuple(b)
+
+
+def launches(g, nsteps: int) -> int:
+    """Kernel launches that step(g, nsteps) issues from the current state."""
+    n = C.c_long()
+    _check(_lib.yf_launches(C.c_void_p(g), int(nsteps), C.byref(n)))
     return n.value
 
 

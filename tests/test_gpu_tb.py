@@ -1,0 +1,179 @@
+"""Variant 4 (two time steps per pass over the inner box, FP32) through the C ABI.
+
+The grid is 170 x 70 x 50 nodes with random lossy materials, a PEC block and PEC sheets that
+cross the box boundary, CPML on five faces, a source plane and two port planes near the x
+ends.  Its box is x 32..127, y 16..55, z 3..39: three tile columns, five tile rows and two
+z segments of the two-step kernel (32 planes, then a ragged 5), surrounded by every kind of
+single-step frame work.  A second geometry moves a port plane to the middle, which splits the
+admissible tile columns (the box takes the longest run of them).
+
+Bars (the FP32 budget used for every variant): fields relative L2 <= 1e-5 against the FP64
+oracle at step 61 (odd: a graph chunk, pairs and one single step); port spectra within 1e-4
+of their maximum.  Against variant 2 on the GPU, over 600 steps (the pulse crosses the box,
+reaches both ports and the absorbing slabs), the same bars.  Graph replay against direct
+pairs and checkpoint resume are bitwise."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import post, yee
+from paper_2208_04371_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BOX = (32, 127, 16, 55, 3, 39)
+
+
+def rel_l2(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _tb_problem(port_mid=False):
+    nx, ny, nz = 170, 70, 50
+    rng = W.SplitMix64(0x7B2)
+    ids = np.array([rng.randint(0, 4) for _ in range(nx * ny * nz)], np.uint8).reshape(nz, ny, nx)
+    ids[20:26, 30:38, 60:75] = 5
+    p = W.Problem(nx=nx, ny=ny, nz=nz, dx=4e-6, dy=5e-6, dz=3e-6, courant=0.95, ids=ids,
+                  eps_r=np.array([1.0, 2.2, 4.0, 9.8, 3.0, 1.0]),
+                  sigma=np.array([0.0, 0.5, 0.0, 20.0, 1e4, 0.0]),
+                  mu_r=np.ones(6), is_pec=np.array([0, 0, 0, 0, 0, 1], np.uint8),
+                  sheets=[(2, 12, 5, 160, 30, 40), (1, 50, 20, 140, 2, 30), (0, 100, 10, 60, 3, 45)],
+                  bc=(1, 1, 1, 1, 0, 1), pml_cells=8, pml_order=3, pml_kappa_max=3.0,
+                  pml_alpha_max=2e8)
+    p.source = W.Source(kind=W.WAVE_DIFF_GAUSS, plane=10, j0=30, j1=40, k0=0, k1=12,
+                        amplitude=2.5, param0=3e-14)
+    second = 90 if port_mid else 150
+    p.ports = [W.Port(plane=16, direction=1, j0=30, j1=40, k0=0, k1=12, kb=12, kt=12, margin=1),
+               W.Port(plane=second, direction=-1, j0=30, j1=40, k0=0, k1=12, kb=12, kt=12,
+                      margin=2)]
+    p.freqs = np.linspace(50e9, 2e12, 37)
+    p.nsteps = 600
+    return p
+
+
+@pytest.fixture(scope="module")
+def tb_ref():
+    p = _tb_problem()
+    return p, yee.run(p, nsteps=61, want_fields=True)
+
+
+def test_box_is_the_documented_one(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
+        assert gpu.tb_box(g.h) == BOX
+    with gpu.Grid(_tb_problem(port_mid=True), prec=gpu.FP32, variant=4) as g:
+        # admissible tile columns: 1 (x 32..63), then 3 and 4 past the port at x = 90
+        assert gpu.tb_box(g.h) == (96, 159, 16, 55, 3, 39)
+
+
+def test_variant4_matches_oracle(gpu, tb_ref):
+    p, ref = tb_ref
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
+        g.step(61)
+        g.sync()
+        f = g.fields()
+        V, I = g.port_dfts()
+    assert rel_l2(f, ref["fields"]) <= 1e-5
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    assert np.max(np.abs(V - Vo)) <= 1e-4 * np.max(np.abs(Vo))
+    assert np.max(np.abs(I - Io)) <= 1e-4 * np.max(np.abs(Io))
+
+
+@pytest.mark.parametrize("port_mid", [False, True])
+def test_variant4_matches_variant2_over_a_long_run(gpu, port_mid):
+    p = _tb_problem(port_mid)
+    out = {}
+    for v in (2, 4):
+        with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
+            g.step(p.nsteps)
+            g.sync()
+            out[v] = (g.fields(), *g.port_dfts())
+    f2, V2, I2 = out[2]
+    f4, V4, I4 = out[4]
+    assert rel_l2(f4, f2) <= 1e-5
+    assert np.max(np.abs(V4 - V2)) <= 1e-4 * np.max(np.abs(V2))
+    assert np.max(np.abs(I4 - I2)) <= 1e-4 * np.max(np.abs(I2))
+
+
+def test_variant_switches_mid_run(gpu):
+    """2 -> 4 -> 2 -> 4 -> 2 with step counts that leave the third buffer current and the
+    auxiliary copy out of step with the buffer index; equals variant 2 throughout."""
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=2) as a, gpu.Grid(p, prec=gpu.FP32, variant=2) as b:
+        a.step(19)
+        for v, n in ((2, 5), (4, 4), (2, 3), (4, 5), (2, 2)):
+            gpu.set_variant(b.h, v)
+            b.step(n)
+        a.sync()
+        b.sync()
+        assert rel_l2(b.fields(), a.fields()) <= 1e-5
+        Va, _ = a.port_dfts()
+        Vb, _ = b.port_dfts()
+    assert np.max(np.abs(Vb - Va)) <= 1e-4 * np.max(np.abs(Va))
+
+
+def test_graph_chunks_equal_direct_pairs(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as a, gpu.Grid(p, prec=gpu.FP32, variant=4) as b:
+        a.step(77)
+        for _ in range(38):
+            b.step(2)
+        b.step(1)
+        assert np.array_equal(a.fields(), b.fields())
+        assert np.array_equal(a.port_dfts()[0], b.port_dfts()[0])
+
+
+def test_launch_count(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
+        pair = gpu.launches(g.h, 2)
+        single = gpu.launches(g.h, 1)
+        assert gpu.launches(g.h, 77) == 38 * pair + single
+        # frame kinds twice, the box kernel, two epilogues
+        assert 5 <= pair <= 13 and 2 <= single <= 6
+
+
+def test_checkpoint_resume_is_bitwise(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as a:
+        a.step(100)
+        full = a.fields()
+        Va, _ = a.port_dfts()
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ck.bin")
+        with gpu.Grid(p, prec=gpu.FP32, variant=4) as b:
+            b.step(50)
+            gpu.checkpoint_save(b.h, path)
+        with gpu.Grid(p, prec=gpu.FP32, variant=4) as c:
+            gpu.checkpoint_load(c.h, path)
+            c.step(50)
+            assert np.array_equal(c.fields(), full)
+            Vc, _ = c.port_dfts()
+    assert np.array_equal(Va, Vc)
+
+
+def test_variant4_rejects_fp64(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP64) as g:
+        with pytest.raises(gpu.YFError):
+            gpu.set_variant(g.h, 4)
+
+
+def test_lossy_line_variant4_matches_variant2_at_full_size(gpu):
+    """The 768 x 384 x 256 lossy line (the timed workload) over 64 steps: the two-step path
+    against the one-step path, fields and port spectra within the FP32 budget."""
+    p = W.config_lossy_line(nsteps=64)
+    out = {}
+    for v in (2, 4):
+        with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
+            if v == 4:
+                assert gpu.tb_box(g.h) == (32, 735, 16, 367, 3, 241)
+            g.step(64)
+            g.sync()
+            out[v] = (g.fields(), *g.port_dfts())
+    f2, V2, I2 = out[2]
+    f4, V4, I4 = out[4]
+    assert rel_l2(f4, f2) <= 1e-5
+    assert np.max(np.abs(V4 - V2)) <= 1e-4 * np.max(np.abs(V2))
