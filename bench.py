@@ -37,11 +37,14 @@ def workload(nz: int = 256):
     return W.config_lossy_line(nz=nz, nsteps=0)
 
 
-def stencil_traffic():
-    """DRAM bytes per step of the stencil from the committed ncu capture, or None when the
-    stencil source has changed since the counters were taken."""
+def stencil_traffic(kernel: str):
+    """DRAM bytes per launch of the dominant stencil kernel from the committed ncu capture
+    (k_yee_tb2: one two-step launch; k_yee_tma_batch: all work kinds of one step), or None
+    when the kernel's source has changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_yee_tma_batch_traffic_lossy_line_768x384x256.json")
+    name = {"k_yee_tb2": "k_yee_tb2_traffic_lossy_line_768x384x256.json",
+            "k_yee_tma_batch": "k_yee_tma_batch_traffic_lossy_line_768x384x256.json"}.get(kernel)
+    path = os.path.join(ROOT, "profiles", name) if name else ""
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -49,7 +52,7 @@ def stencil_traffic():
         f = os.path.join(ROOT, rel)
         if not os.path.exists(f) or hashlib.sha256(open(f, "rb").read()).hexdigest() != digest:
             return None
-    return d["dram_bytes_per_step"]
+    return d["dram_bytes_per_launch"] if "dram_bytes_per_launch" in d else d["dram_bytes_per_step"]
 
 
 def peaks():
@@ -256,9 +259,11 @@ def run_ours(args, rank, world, local_rank):
 
     p = workload(args.nz)
     stream = torch.cuda.Stream()
-    g = yf.Grid(p, prec=yf.FP32, stream=stream.cuda_stream)
+    kseg = args.kseg or (32 if args.variant == 4 else 16)
+    g = yf.Grid(p, prec=yf.FP32, stream=stream.cuda_stream, variant=args.variant, kseg=kseg)
     chunk = args.chunk
-    launches_per_step = yf.launches_per_step(g.h)
+    launches_per_bench_step = yf.launches(g.h, chunk)
+    box = yf.tb_box(g.h) if args.variant == 4 else None
     for _ in range(args.warmup):
         g.step(chunk)
     g.sync()
@@ -289,18 +294,27 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel durations (CUDA events around every launch, same stream, right after the
     # timed region) for the roofline of the stencil
     prof = yf.profile_steps(g.h, chunk)
-    fused = [k for k in prof if k.startswith("k_yee_")]
-    if fused:
-        stencil_ms, kname = prof[fused[0]], fused[0]
-    else:
-        stencil_ms, kname = prof["k_update_h"] + prof["k_update_e"], "k_update_h + k_update_e"
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_CELL_FP32 * p.cells / (stencil_ms / 1e3) / 1e9
+    if args.variant == 4:
+        # the two-step box kernel: 51 B per box node per launch (step n read once, step n+2
+        # written once) for two cell updates
+        kname = "k_yee_tb2"
+        nodes = (box[1] - box[0] + 1) * (box[3] - box[2] + 1) * (box[5] - box[4] + 1) if box else 0
+        algo = BYTES_PER_CELL_FP32 * nodes
+        unit_note = "bytes per launch (two time steps of the inner box)"
+    else:
+        fused = [k for k in prof if k.startswith("k_yee_")]
+        kname = fused[0] if fused else "k_update_h + k_update_e"
+        algo = BYTES_PER_CELL_FP32 * p.cells
+        unit_note = "bytes per step (all work kinds)"
+    stencil_ms = prof[kname] if kname in prof else prof["k_update_h"] + prof["k_update_e"]
+    achieved = algo / (stencil_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": stencil_traffic() if (args.nz == 256 and kname == "k_yee_tma_batch") else None,
-            "traffic_unit": "bytes per step (all work kinds)",
+            "traffic": stencil_traffic(kname) if args.nz == 256 else None,
+            "traffic_unit": unit_note,
+            "algorithmic_bytes": algo,
             "bytes_per_cell_update": BYTES_PER_CELL_FP32,
             "kernel_ms": prof}
 
@@ -339,12 +353,13 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": p.name, "cells": p.cells, "steps_per_bench_step": chunk,
+                       "variant": args.variant, "tile_y": 8, "kseg": kseg, "inner_box": box,
                        "l2": "inputs larger than L2 (1.8 GB of fields)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * chunk * args.steps,
+            "gpu_launches": launches_per_bench_step * args.steps,
             "clocks": clocks,
             "batched": batched,
             "surrogate": sur,
@@ -358,6 +373,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--variant", type=int, default=4, choices=[2, 4],
+                    help="stencil variant: 4 two-step inner box (default), 2 one step per pass")
+    ap.add_argument("--kseg", type=int, default=0,
+                    help="z-planes per one-step block (0: 32 for variant 4, 16 for variant 2)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -165,7 +165,8 @@ yf_status yf_set_dft_mode(yf_grid *g, int mask);
  *      from step n to n+2 in a single read of step n, while variant 2's kernels advance the
  *      rest of the grid one step at a time, with the port epilogue after each step.  Uses a
  *      third field buffer (6 (nz+1)(ny+1) px words more, px = nx+1 rounded up to 32, allocated here or at the first step and
- *      freed when another variant is set).  An odd remaining step runs as variant 2.
+ *      freed when another variant is set).  An odd remaining step runs as variant 2.  The
+ *      two-step blocks take min(64, 2 kseg) z-planes each.
  * tile_y in {4, 8, 16}, 1 <= kseg <= 64.  All variants compute the same update; results agree to
  * rounding.  Drops captured graphs; may be called between steps.  YF_E_INVALID for variant 4
  * on an FP64 grid or on one with 6 (nz+1)(ny+1) px >= 2^31 (32-bit offsets in its kernel). */
@@ -282,7 +283,10 @@ yf_status yf_reset(yf_grid *g);
 
 /* Tracing: run n steps without graphs, bracketing every kernel launch with CUDA events
  * on the handle's stream, and return the mean duration in ms per launch of each kernel
- * of a step (names via yf_kernel_name).  *nkern receives the number of kernels (<= 8). */
+ * of a step (names via yf_kernel_name).  *nkern receives the number of kernels (<= 8).
+ * Variant 4 runs max(1, n/2) pairs of steps and reports the box kernel (timed on its own
+ * stream, one launch per pair), the frame step (all its work kinds, two per pair) and the
+ * epilogue; the box kernel overlaps the first frame step, so its time includes that sharing. */
 yf_status yf_profile_steps(yf_grid *g, long n, double *ms_per_launch, int *nkern);
 const char *yf_kernel_name(yf_grid *g, int idx);
 

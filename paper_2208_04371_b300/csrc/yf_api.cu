@@ -956,11 +956,7 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
 {
     cudaError_t e;
     cudaEventRecord(ev[0], g->stream);
-    if (g->variant == 4) {
-        if ((e = tb_single(g, g->stream)) != cudaSuccess) return e;
-        cudaEventRecord(ev[1], g->stream);
-        *nk = 2;
-    } else if (g->variant >= 1) {
+    if (g->variant >= 1) {
         if (g->variant == 3)
             e = launch_skew<T>(fused_args<T>(g), g->tmF[g->cur], g->tmC, g->tile_y, g->status, g->stream);
         else if (g->variant == 2)
@@ -986,11 +982,39 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
     return e;
 }
 
+// variant 4: pairs of steps; per launch the box kernel (one per pair), the frame step and the
+// epilogue (two each per pair)
+static yf_status profile_tb(yf_grid *g, long n, double *ms, int *nkern)
+{
+    cudaEvent_t ev[8];
+    for (int q = 0; q < 8; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
+    const long pairs = n < 2 ? 1 : n / 2;
+    double acc[3] = {0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (long t = 0; t < pairs && e == cudaSuccess; ++t) {
+        e = tb_pair(g, g->stream, ev);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
+        float m[5] = {0, 0, 0, 0, 0};
+        const int from[5] = {0, 2, 3, 5, 6}, to[5] = {1, 3, 4, 6, 7};
+        for (int q = 0; q < 5 && e == cudaSuccess; ++q) e = cudaEventElapsedTime(&m[q], ev[from[q]], ev[to[q]]);
+        acc[0] += m[0];
+        acc[1] += 0.5 * (m[1] + m[3]);
+        acc[2] += 0.5 * (m[2] + m[4]);
+    }
+    for (int q = 0; q < 8; ++q) cudaEventDestroy(ev[q]);
+    YF_CUDA_TRY(e);
+    g->steps_done += 2 * pairs;
+    for (int q = 0; q < 3; ++q) ms[q] = acc[q] / (double)pairs;
+    *nkern = 3;
+    return YF_OK;
+}
+
 extern "C" yf_status yf_profile_steps(yf_grid *g, long n, double *ms, int *nkern)
 {
     if (!g || !ms || !nkern || n < 1) return fail(YF_E_INVALID, "yf_profile_steps: bad argument");
     yf_status st = finalize(g);
     if (st != YF_OK) return st;
+    if (g->variant == 4) return profile_tb(g, n, ms, nkern);
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
     double acc[3] = {0, 0, 0};
@@ -1021,10 +1045,12 @@ const char *yf_kernel_name(yf_grid *g, int idx)
     static const char *fused[] = {"k_yee_fused", "k_epilogue"};
     static const char *tma[] = {"k_yee_tma_batch", "k_epilogue"};
     static const char *skew[] = {"k_yee_skew", "k_epilogue"};
+    static const char *tb[] = {"k_yee_tb2", "k_yee_tma_batch", "k_epilogue"};
     if (!g) return "";
+    if (g->variant == 4) return (idx >= 0 && idx < 3) ? tb[idx] : "";
     if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
     if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
-    if (g->variant == 2 || g->variant == 4) return (idx >= 0 && idx < 2) ? tma[idx] : "";
+    if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";
     return (idx >= 0 && idx < 3) ? ref[idx] : "";
 }
 

@@ -331,7 +331,6 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     }
 }
 
-constexpr int kTbSeg = 32;   // z-planes per two-step block
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder()
 {
@@ -471,11 +470,14 @@ yf_status tb_build(yf_grid *g)
             if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
             if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
         }
+    // z-planes per two-step block: twice the one-step segment (the two-step block re-reads four
+    // halo planes instead of two), at most the one-step kernels' limit
+    const int seg = std::min(kMaxKseg, 2 * g->kseg);
     if (have_box)
-        for (int kb = B[4]; kb <= B[5]; kb += kTbSeg)
+        for (int kb = B[4]; kb <= B[5]; kb += seg)
             for (int j0 = B[2]; j0 <= B[3]; j0 += TBY)
                 for (int i0 = B[0]; i0 <= B[1]; i0 += TBX)
-                    two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + kTbSeg - 1)});
+                    two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + seg - 1)});
     yf_status st;
     if ((st = upload_items(full, &t->full)) != YF_OK) return bail(st);
     if ((st = upload_items(frame, &t->frame)) != YF_OK) return bail(st);
@@ -567,28 +569,41 @@ cudaError_t tb_single(yf_grid *g, cudaStream_t s)
 // two time steps with both epilogues: the box n -> n+2 on a side stream, concurrently the
 // frame n -> n+1 and its epilogue; then, once the box is done, the frame n+1 -> n+2 and its
 // epilogue
-cudaError_t tb_pair(yf_grid *g, cudaStream_t s)
+// ev (tracing, may be null): 8 events recorded around the box kernel on its stream (0, 1) and
+// around each frame step and epilogue on s (2..4 first step, 5..7 second)
+cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
 {
     TbPlan &t = *g->tb;
     const int r = g->cur, h = g->hpar, r1 = (r + 1) % 3;
     cudaError_t e;
     const bool box = t.count > 0;
+    auto mark = [&](int q, cudaStream_t st) { return ev ? cudaEventRecord(ev[q], st) : cudaSuccess; };
     if (box) {
         if ((e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(t.stream, t.fork, 0)) != cudaSuccess) return e;
+        if ((e = mark(0, t.stream)) != cudaSuccess) return e;
         if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
+        if ((e = mark(1, t.stream)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(t.join, t.stream)) != cudaSuccess) return e;
+    } else if (ev) {
+        if ((e = mark(0, s)) != cudaSuccess || (e = mark(1, s)) != cudaSuccess) return e;
     }
+    if ((e = mark(2, s)) != cudaSuccess) return e;
     if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r + h, g->status, s, &g->side)) != cudaSuccess) return e;
     g->cur = r1;
     g->hpar = h ^ 1;
+    if ((e = mark(3, s)) != cudaSuccess) return e;
     if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
+    if ((e = mark(4, s)) != cudaSuccess) return e;
     if (box && (e = cudaStreamWaitEvent(s, t.join, 0)) != cudaSuccess) return e;
+    if ((e = mark(5, s)) != cudaSuccess) return e;
     if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r1 + (h ^ 1), g->status, s, &g->side)) != cudaSuccess)
         return e;
     g->cur = (r + 2) % 3;
     g->hpar = h;
-    return launch_epilogue<float>(epi_params<float>(g), s);
+    if ((e = mark(6, s)) != cudaSuccess) return e;
+    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
+    return mark(7, s);
 }
 
 int tb_launches_pair(const yf_grid *g)

@@ -31,7 +31,8 @@ def test_reference_arm_prints_one_contract_line():
 def test_stored_traffic_is_dropped_when_the_stencil_changes(tmp_path, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.stencil_traffic() is not None          # committed capture matches the source
+    assert bench.stencil_traffic("k_yee_tma_batch") is not None   # committed captures match the sources
+    assert bench.stencil_traffic("k_yee_tb2") is not None
     # a copy of the tree whose stencil source differs by one byte
     fake = tmp_path / "root"
     (fake / "profiles").mkdir(parents=True)
@@ -41,4 +42,4 @@ def test_stored_traffic_is_dropped_when_the_stencil_changes(tmp_path, monkeypatc
     src = open(os.path.join(ROOT, "paper_2208_04371_b300", "csrc", "yf_tma.cu"), "rb").read()
     (fake / "paper_2208_04371_b300" / "csrc" / "yf_tma.cu").write_bytes(src + b"\n")
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    assert bench.stencil_traffic() is None
+    assert bench.stencil_traffic("k_yee_tma_batch") is None
