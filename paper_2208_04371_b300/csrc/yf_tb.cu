@@ -156,13 +156,19 @@ struct Coef {
 
 // H update of a node pair (S1 from step-n data, S3 from E^{n+1}): e0/e1 = E on planes p, p+1,
 // h0 = H on plane p, all in window layout; result into hw
+// A thread keeps its stage and pair on every plane, so the E_x, E_y (or H_x, H_y) of the
+// pair that one plane reads as its upper (lower) z-neighbour are the next plane's centre
+// values: they are carried in registers (cx, cy) once the stage has run on a plane before.
 __device__ __forceinline__ void h_pair(const float *e0, const float *e1, const float *h0, float *hw, int w,
-                                       const Coef &K)
+                                       const Coef &K, float2 &cx, float2 &cy, bool carried)
 {
-    const float2 ex = ld2(e0 + w), ey = ld2(e0 + WN + w), ez = ld2(e0 + 2 * WN + w);
+    const float2 ex = carried ? cx : ld2(e0 + w), ey = carried ? cy : ld2(e0 + WN + w);
+    const float2 ez = ld2(e0 + 2 * WN + w);
     const float2 exU = ld2(e0 + w + WXN), ezU = ld2(e0 + 2 * WN + w + WXN);
     const float2 eyR = make_float2(ey.y, e0[WN + w + 2]), ezR = make_float2(ez.y, e0[2 * WN + w + 2]);
     const float2 ex1 = ld2(e1 + w), ey1 = ld2(e1 + WN + w);
+    cx = ex1;
+    cy = ey1;
     // H_x -= dt/mu0 (dEz/dy - dEy/dz), H_y -= dt/mu0 (dEx/dz - dEz/dx), H_z -= dt/mu0 (dEy/dx - dEx/dy)
     st2(hw + w, __ffma2_rn(curl(dif(ezU, ez), K.ry, dif(ey1, ey), K.nrz), K.ndb, ld2(h0 + w)));
     st2(hw + WN + w, __ffma2_rn(curl(dif(ex1, ex), K.rz, dif(ezR, ez), K.nrx), K.ndb, ld2(h0 + WN + w)));
@@ -173,12 +179,14 @@ __device__ __forceinline__ void h_pair(const float *e0, const float *e1, const f
 // plane k.  Class 0 (PEC) has Ca = Cb = 0, so its edges stay zero.
 __device__ __forceinline__ void e_pair(const float *eo, const float *ha, const float *hp, const unsigned char *cl,
                                        const float2 *CT, int w, int c, const Coef &K, float2 *vx, float2 *vy,
-                                       float2 *vz)
+                                       float2 *vz, float2 &cx, float2 &cy, bool carried)
 {
     const float2 hx = ld2(ha + w), hy = ld2(ha + WN + w), hz = ld2(ha + 2 * WN + w);
     const float2 hxD = ld2(ha + w - WXN), hzD = ld2(ha + 2 * WN + w - WXN);
     const float2 hyL = make_float2(ha[WN + w - 1], hy.x), hzL = make_float2(ha[2 * WN + w - 1], hz.x);
-    const float2 hpx = ld2(hp + w), hpy = ld2(hp + WN + w);
+    const float2 hpx = carried ? cx : ld2(hp + w), hpy = carried ? cy : ld2(hp + WN + w);
+    cx = hx;
+    cy = hy;
     const unsigned cxx = *reinterpret_cast<const unsigned short *>(cl + c);
     const unsigned cyy = *reinterpret_cast<const unsigned short *>(cl + CN + c);
     const unsigned czz = *reinterpret_cast<const unsigned short *>(cl + 2 * CN + c);
@@ -262,6 +270,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     const bool xy_edge = i0 == P.bx0 || i0 + TBX - 1 == P.bx1 || j0 == P.by0 || j0 + TBY - 1 == P.by1;
     // ring slots of plane q-1: a = (q-1) mod 3 (H^{n+1/2}, E^{n+1}), b = (q-1) mod 6 (classes)
     int a = (kb - 2) % 3, b = (kb - 2) % CSL;
+    float2 c1x = make_float2(0.f, 0.f), c1y = c1x, c2x = c1x, c2y = c1x;   // carried z-neighbours
 
     for (int q = kb - 1; q <= ke + 3; ++q) {
         if (q <= ke + 2) {
@@ -292,13 +301,13 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         const unsigned char *cl3 = sm + C_OFF + (b >= 2 ? b - 2 : b + 4) * 3 * CN;
 
         // phase 1: S1 on plane q-1, S3 on plane q-3
-        if (T1.kind == 1 && q <= ke + 2) h_pair(f0, f1, f0 + 3 * WN, haw, T1.w, K);
-        if (T1.kind == 3 && q >= kb + 2) h_pair(ea3, ea2, ha3, hb3, T1.w, K);
+        if (T1.kind == 1 && q <= ke + 2) h_pair(f0, f1, f0 + 3 * WN, haw, T1.w, K, c1x, c1y, q > kb - 1);
+        if (T1.kind == 3 && q >= kb + 2) h_pair(ea3, ea2, ha3, hb3, T1.w, K, c1x, c1y, q > kb + 2);
         __syncthreads();
         // phase 2: S2 on plane q-1, S4 on plane q-3 (into C)
         if (T2.kind == 2 && q >= kb && q <= ke + 2) {
             float2 vx, vy, vz;
-            e_pair(f0, haw, hap, cl1, CT, T2.w, T2.c, K, &vx, &vy, &vz);
+            e_pair(f0, haw, hap, cl1, CT, T2.w, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb);
             st2(eaw + T2.w, vx);
             st2(eaw + WN + T2.w, vy);
             st2(eaw + 2 * WN + T2.w, vz);
@@ -317,7 +326,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         }
         if (T2.kind == 4 && q >= kb + 3) {
             float2 vx, vy, vz;
-            e_pair(ea3, hb3, hb4, cl3, CT, T2.w, T2.c, K, &vx, &vy, &vz);
+            e_pair(ea3, hb3, hb4, cl3, CT, T2.w, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb + 3);
             float *C = P.C + (p3 * plane + T2.g);
             st2(C, vx);
             st2(C + npts, vy);
