@@ -177,3 +177,24 @@ def test_lossy_line_variant4_matches_variant2_at_full_size(gpu):
     f4, V4, I4 = out[4]
     assert rel_l2(f4, f2) <= 1e-5
     assert np.max(np.abs(V4 - V2)) <= 1e-4 * np.max(np.abs(V2))
+
+
+def test_grid_without_a_box_steps_exactly_like_variant2(gpu):
+    """A grid too small for a box: every pair is two whole-grid one-step passes, the same
+    launches as variant 2, so the fields agree bit for bit."""
+    p = _tb_problem()
+    p.nx = 60
+    p.ids = p.ids[:, :, :60].copy()
+    p.sheets = [(2, 12, 5, 50, 30, 40)]
+    p.ports = [W.Port(plane=16, direction=1, j0=30, j1=40, k0=0, k1=12, kb=12, kt=12, margin=1),
+               W.Port(plane=44, direction=-1, j0=30, j1=40, k0=0, k1=12, kb=12, kt=12, margin=1)]
+    out = {}
+    for v in (2, 4):
+        with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
+            if v == 4:
+                assert gpu.tb_box(g.h) is None
+            g.step(37)
+            g.sync()
+            out[v] = g.fields()
+    assert np.array_equal(out[2], out[4])
+
