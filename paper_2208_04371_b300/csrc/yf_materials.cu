@@ -40,28 +40,58 @@ __device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
     a = lo; b = hi;
 }
 
-// key of edge `comp` at node (i, j, k); kEmpty for PEC / wall / non-existent edges
-__device__ uint32_t edge_key(const KeyArgs &A, int comp, int i, int j, int k)
+// The material ids of the cells around node (i, j, k) at offsets (di, dj, dk) in {-1, 0}^3:
+// the three E edges of the node use seven of the eight (all but (-1, -1, -1)); a cell outside
+// the grid reads as 0 and is never used (its edges are walls).
+struct NodeCells {
+    uint32_t c000, c100, c010, c001, c110, c101, c011;   // c<-di><-dj><-dk>: 1 = offset -1
+};
+
+__device__ __forceinline__ NodeCells node_cells(const KeyArgs &A, int i, int j, int k)
 {
-    int c[4][3];
-    if (comp == 0) {            // E_x(i+1/2, j, k)
-        if (i >= A.nx || j < 1 || j >= A.ny || k < 1 || k >= A.nz) return kEmpty;
-        int t[4][3] = {{i, j - 1, k - 1}, {i, j, k - 1}, {i, j - 1, k}, {i, j, k}};
-        memcpy(c, t, sizeof(c));
-    } else if (comp == 1) {     // E_y(i, j+1/2, k)
-        if (i < 1 || i >= A.nx || j >= A.ny || k < 1 || k >= A.nz) return kEmpty;
-        int t[4][3] = {{i - 1, j, k - 1}, {i, j, k - 1}, {i - 1, j, k}, {i, j, k}};
-        memcpy(c, t, sizeof(c));
-    } else {                    // E_z(i, j, k+1/2)
-        if (i < 1 || i >= A.nx || j < 1 || j >= A.ny || k >= A.nz) return kEmpty;
-        int t[4][3] = {{i - 1, j - 1, k}, {i, j - 1, k}, {i - 1, j, k}, {i, j, k}};
-        memcpy(c, t, sizeof(c));
+    const long sy = A.nx, sz = (long)A.nx * A.ny;
+    const long c = (long)k * sz + (long)j * sy + i;
+    const bool in = i < A.nx && j < A.ny && k < A.nz;
+    const bool im = i >= 1, jm = j >= 1, km = k >= 1;
+    const bool xi = i < A.nx && i >= 0, yj = j < A.ny, zk = k < A.nz;
+    NodeCells n;
+    n.c000 = in ? A.ids[c] : 0;
+    n.c100 = (im && yj && zk) ? A.ids[c - 1] : 0;
+    n.c010 = (xi && jm && zk) ? A.ids[c - sy] : 0;
+    n.c001 = (xi && yj && km) ? A.ids[c - sz] : 0;
+    n.c110 = (im && jm && zk) ? A.ids[c - 1 - sy] : 0;
+    n.c101 = (im && yj && km) ? A.ids[c - 1 - sz] : 0;
+    n.c011 = (xi && jm && km) ? A.ids[c - sy - sz] : 0;
+    return n;
+}
+
+// the four cell ids of edge `comp` at node (i, j, k); false for wall and non-existent edges
+__device__ __forceinline__ bool edge_ids(const KeyArgs &A, const NodeCells &n, int comp, int i, int j, int k,
+                                         uint32_t id[4])
+{
+    if (comp == 0) {            // E_x(i+1/2, j, k): cells at dj, dk in {-1, 0}
+        if (i >= A.nx || j < 1 || j >= A.ny || k < 1 || k >= A.nz) return false;
+        id[0] = n.c011; id[1] = n.c001; id[2] = n.c010; id[3] = n.c000;
+    } else if (comp == 1) {     // E_y(i, j+1/2, k): cells at di, dk in {-1, 0}
+        if (i < 1 || i >= A.nx || j >= A.ny || k < 1 || k >= A.nz) return false;
+        id[0] = n.c101; id[1] = n.c001; id[2] = n.c100; id[3] = n.c000;
+    } else {                    // E_z(i, j, k+1/2): cells at di, dj in {-1, 0}
+        if (i < 1 || i >= A.nx || j < 1 || j >= A.ny || k >= A.nz) return false;
+        id[0] = n.c110; id[1] = n.c010; id[2] = n.c100; id[3] = n.c000;
     }
-    uint32_t id[4];
+    return true;
+}
+
+__device__ __forceinline__ bool uniform(const uint32_t id[4]) { return id[0] == id[1] && id[1] == id[2] && id[2] == id[3]; }
+
+// key of an edge from its four cell ids: kEmpty when one of them is PEC (pec is the block's
+// shared copy of the per-material flags)
+__device__ __forceinline__ uint32_t key_of(const KeyArgs &A, const uint8_t *pec, uint32_t id[4])
+{
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-        id[q] = A.ids[((long)c[q][2] * A.ny + c[q][1]) * A.nx + c[q][0]];
         if ((int)id[q] >= A.nmat) { atomicOr(A.overflow, 2); return kEmpty; }
-        if (A.pec[id[q]]) return kEmpty;
+        if (pec[id[q]]) return kEmpty;
     }
     cswap(id[0], id[1]); cswap(id[2], id[3]); cswap(id[0], id[2]); cswap(id[1], id[3]);
     cswap(id[1], id[2]);
@@ -73,64 +103,101 @@ __device__ __forceinline__ uint32_t hash_slot(uint32_t key)
     return (key * 2654435761u) >> (32 - kHashBits);
 }
 
-__global__ void k_collect(KeyArgs A, uint32_t *table, int *overflow)
+constexpr int kCache = 64;   // per-block direct-mapped cache of keys (classes) already handled
+
+// Both passes run over nodes (i, j, k): a block's threads stride along the row i, blocks
+// stride over rows j (grid y) and planes k (grid z); about a thousand resident blocks, so that
+// each keeps its caches over many rows.
+__device__ __forceinline__ void load_pec(const KeyArgs &A, uint8_t *pec)
 {
-    const long npts = A.plane * (A.nz + 1);
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < npts;
-         q += (long)gridDim.x * blockDim.x) {
-        const int k = (int)(q / A.plane);
-        const int r = (int)(q % A.plane);
-        const int j = r / A.px, i = r % A.px;
-        if (i > A.nx || j > A.ny) continue;
-        for (int comp = 0; comp < 3; ++comp) {
-            const uint32_t key = edge_key(A, comp, i, j, k);
-            // a handful of distinct keys among millions of edges: one lane per distinct key
-            // of the warp inserts, and a slot is read before any compare-and-swap, so the set
-            // fills with a few atomics instead of one contended atomic per edge
-            const unsigned active = __activemask();
-            const unsigned peers = __match_any_sync(active, key);
-            if (key == kEmpty || (int)(__ffs(peers) - 1) != (int)(threadIdx.x & 31)) continue;
-            uint32_t s = hash_slot(key);
-            for (int probes = 0;; ++probes) {
-                if (probes >= kHashSize) { atomicOr(overflow, 1); break; }
-                const uint32_t cur = *(volatile const uint32_t *)&table[s];
-                if (cur == key) break;
-                if (cur == kEmpty) {
-                    const uint32_t prev = atomicCAS(&table[s], kEmpty, key);
-                    if (prev == kEmpty || prev == key) break;
-                }
-                s = (s + 1) & (kHashSize - 1);
-            }
-        }
-    }
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) pec[q] = A.pec[q];
 }
 
-__global__ void k_assign(KeyArgs A, const uint32_t *table, const uint8_t *slot_class,
-                         uint8_t *cx, uint8_t *cy, uint8_t *cz)
+__global__ void k_collect(KeyArgs A, uint32_t *table, int *overflow)
 {
-    const long npts = A.plane * (A.nz + 1);
+    __shared__ uint8_t pec[256];
+    __shared__ uint32_t seen[kCache];   // keys this block has already put into the set
+    __shared__ unsigned useen[8];       // the same for uniform keys (four equal ids), by id
+    load_pec(A, pec);
+    for (int q = threadIdx.x; q < kCache; q += blockDim.x) seen[q] = kEmpty;
+    if (threadIdx.x < 8) useen[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int k = blockIdx.z; k <= A.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j <= A.ny; j += gridDim.y)
+        for (int i = threadIdx.x; i <= A.nx; i += blockDim.x) {
+            const NodeCells n = node_cells(A, i, j, k);
+            for (int comp = 0; comp < 3; ++comp) {
+                uint32_t id[4];
+                if (!edge_ids(A, n, comp, i, j, k, id)) continue;
+                const bool uni = uniform(id);
+                if (uni && (useen[id[0] >> 5] >> (id[0] & 31) & 1u)) continue;
+                const uint32_t key = key_of(A, pec, id);
+                if (key == kEmpty) continue;
+                // a handful of distinct keys among millions of edges: after its first
+                // insertion a key is found in the block's cache; the set's slot is read
+                // before any compare-and-swap, so racing first insertions stay cheap
+                const int c = (key * 2654435761u) >> (32 - 6);
+                if (seen[c] == key) continue;
+                uint32_t s = hash_slot(key);
+                for (int probes = 0;; ++probes) {
+                    if (probes >= kHashSize) { atomicOr(overflow, 1); break; }
+                    const uint32_t cur = *(volatile const uint32_t *)&table[s];
+                    if (cur == key) break;
+                    if (cur == kEmpty) {
+                        const uint32_t prev = atomicCAS(&table[s], kEmpty, key);
+                        if (prev == kEmpty || prev == key) break;
+                    }
+                    s = (s + 1) & (kHashSize - 1);
+                }
+                if (uni) atomicOr(&useen[id[0] >> 5], 1u << (id[0] & 31));
+                else seen[c] = key;
+            }
+        }
+}
+
+// uni_class[m]: class of an edge whose four cells are all material m (0 for PEC or absent)
+__global__ void k_assign(KeyArgs A, const uint32_t *__restrict__ table, const uint8_t *__restrict__ slot_class,
+                         const uint8_t *__restrict__ uni_class, uint8_t *cx, uint8_t *cy, uint8_t *cz)
+{
+    __shared__ uint8_t pec[256], uni[256];
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) uni[q] = uni_class[q];
+    // (class << 32) | key, one 64-bit word so that a reader never pairs a key with another's class
+    __shared__ unsigned long long cache[kCache];
+    load_pec(A, pec);
+    for (int q = threadIdx.x; q < kCache; q += blockDim.x) cache[q] = kEmpty;
+    __syncthreads();
     uint8_t *out[3] = {cx, cy, cz};
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < npts;
-         q += (long)gridDim.x * blockDim.x) {
-        const int k = (int)(q / A.plane);
-        const int r = (int)(q % A.plane);
-        const int j = r / A.px, i = r % A.px;
-        for (int comp = 0; comp < 3; ++comp) {
-            uint8_t cl = 0;
-            if (i <= A.nx && j <= A.ny) {
-                const uint32_t key = edge_key(A, comp, i, j, k);
+    for (int k = blockIdx.z; k <= A.nz; k += gridDim.z)
+        for (int j = blockIdx.y; j <= A.ny; j += gridDim.y)
+        for (int i = threadIdx.x; i < A.px; i += blockDim.x) {
+            const long q = (long)k * A.plane + (long)j * A.px + i;
+            const NodeCells n = i <= A.nx ? node_cells(A, i, j, k) : NodeCells{0, 0, 0, 0, 0, 0, 0};
+            for (int comp = 0; comp < 3; ++comp) {
+                uint8_t cl = 0;
+                uint32_t id[4];
+                const bool live = i <= A.nx && edge_ids(A, n, comp, i, j, k, id);
+                const bool flat = live && uniform(id);
+                if (flat) cl = uni[id[0]];
+                const uint32_t key = (live && !flat) ? key_of(A, pec, id) : kEmpty;
                 if (key != kEmpty) {
-                    uint32_t s = hash_slot(key);
-                    for (int probes = 0; probes < kHashSize; ++probes) {
-                        if (table[s] == key) { cl = slot_class[s]; break; }
-                        if (table[s] == kEmpty) break;
-                        s = (s + 1) & (kHashSize - 1);
+                    const int c = (key * 2654435761u) >> (32 - 6);
+                    const unsigned long long e = cache[c];
+                    if ((uint32_t)e == key) {
+                        cl = (uint8_t)(e >> 32);
+                    } else {
+                        uint32_t s = hash_slot(key);
+                        for (int probes = 0; probes < kHashSize; ++probes) {
+                            const uint32_t t = __ldg(&table[s]);
+                            if (t == key) { cl = __ldg(&slot_class[s]); break; }
+                            if (t == kEmpty) break;
+                            s = (s + 1) & (kHashSize - 1);
+                        }
+                        cache[c] = ((unsigned long long)cl << 32) | key;
                     }
                 }
+                out[comp][q] = cl;
             }
-            out[comp][q] = cl;
         }
-    }
 }
 
 // zero-thickness sheet: class 0 on the in-plane edges (see yf_add_pec_sheet)
@@ -163,15 +230,18 @@ yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const 
     for (int m = 0; m < nmat; ++m) pec_h[m] = is_pec ? (is_pec[m] ? 1 : 0) : 0;
 
     uint32_t *table = nullptr;
-    uint8_t *slot_class = nullptr, *pec_d = nullptr;
+    uint8_t *slot_class = nullptr, *pec_d = nullptr, *uni_d = nullptr;
+    std::vector<uint8_t> uni_h(256, 0);
     int *overflow = nullptr;
     yf_status st = YF_OK;
     std::vector<uint32_t> keys(kHashSize);
     std::vector<uint8_t> slot_h(kHashSize, 0);
     KeyArgs A;
     int ovf = 0;
+    const dim3 blk(256), grd(1, std::min(ny + 1, 128), std::min(nz + 1, 8));
     if (cudaMalloc(&table, kHashSize * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&slot_class, kHashSize) != cudaSuccess || cudaMalloc(&pec_d, 256) != cudaSuccess ||
+        cudaMalloc(&uni_d, 256) != cudaSuccess ||
         cudaMalloc(&overflow, sizeof(int)) != cudaSuccess) {
         st = fail(YF_E_OOM, "derive_edge_classes: device allocation failed");
         goto done;
@@ -183,7 +253,7 @@ yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const 
         goto done;
     }
     A.ids = ids_dev; A.pec = pec_d; A.nmat = nmat; A.overflow = overflow; A.nx = nx; A.ny = ny; A.nz = nz; A.px = px; A.plane = plane;
-    k_collect<<<1184, 256, 0, s>>>(A, table, overflow);
+    k_collect<<<grd, blk, 0, s>>>(A, table, overflow);
     if (cudaMemcpyAsync(keys.data(), table, kHashSize * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                         s) != cudaSuccess ||
         cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -232,13 +302,18 @@ yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const 
         }
         res->nclass = next;
         for (auto &sv : slot_val) slot_h[sv.first] = (uint8_t)uniq[sv.second];
+        for (int sl = 0; sl < kHashSize; ++sl) {
+            const uint32_t key = keys[sl];
+            const uint32_t m = key & 0xFF;
+            if (key != kEmpty && key == m * 0x01010101u) uni_h[m] = slot_h[sl];
+        }
     }
-    if (cudaMemcpyAsync(slot_class, slot_h.data(), kHashSize, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess) {
+    if (cudaMemcpyAsync(slot_class, slot_h.data(), kHashSize, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(uni_d, uni_h.data(), 256, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         st = fail(YF_E_CUDA, "derive_edge_classes: upload failed");
         goto done;
     }
-    k_assign<<<1184, 256, 0, s>>>(A, table, slot_class, cls_dev[0], cls_dev[1], cls_dev[2]);
+    k_assign<<<grd, blk, 0, s>>>(A, table, slot_class, uni_d, cls_dev[0], cls_dev[1], cls_dev[2]);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         st = fail(YF_E_CUDA, "derive_edge_classes: class assignment failed");
         goto done;
@@ -247,6 +322,7 @@ done:
     if (table) cudaFree(table);
     if (slot_class) cudaFree(slot_class);
     if (pec_d) cudaFree(pec_d);
+    if (uni_d) cudaFree(uni_d);
     if (overflow) cudaFree(overflow);
     return st;
 }
