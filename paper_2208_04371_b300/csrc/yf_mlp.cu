@@ -156,6 +156,36 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 }
 
 // 32 lanes x 32 consecutive FP32 columns: thread t of the warp gets lane (base lane + t)
+// 32 columns of one accumulator row per thread, without waiting: the registers are valid only
+// after tmem_wait32 on the same array
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+// wait for this thread's outstanding TMEM loads; the array is an operand so that no use of it
+// is scheduled before the wait
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                   "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                   "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile(
@@ -273,6 +303,66 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs &g, const uint32_t (&r)
     if (g.out_t) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) g.out_t[(size_t)(q + i) * g.ld_t + row] = __float2bfloat16_rn(v[i]);
+    }
+}
+
+// Hidden-layer epilogue with only the BF16 activations to write (the inference path): bias,
+// GELU, then the warp's 32 x 32 chunk goes through its shared-memory staging area (rows of
+// 80 bytes: a quarter-warp's 16-byte writes hit distinct banks) so that each global store
+// instruction writes 8 rows of 64 contiguous bytes instead of 32 rows of 16.
+constexpr int kStageRow = 80;
+__device__ __forceinline__ void epi_hidden_staged(const GemmArgs &g, const uint32_t (&r)[32], int row0, int lane,
+                                                  int q, const float *bias, uint8_t *stg)
+{
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 b4 = reinterpret_cast<const float4 *>(bias + q)[i];
+        v[4 * i] = gelu(__uint_as_float(r[4 * i]) + b4.x);
+        v[4 * i + 1] = gelu(__uint_as_float(r[4 * i + 1]) + b4.y);
+        v[4 * i + 2] = gelu(__uint_as_float(r[4 * i + 2]) + b4.z);
+        v[4 * i + 3] = gelu(__uint_as_float(r[4 * i + 3]) + b4.w);
+    }
+    uint4 *srow = reinterpret_cast<uint4 *>(stg + lane * kStageRow);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        srow[j] = make_uint4(pack_bf16(v[8 * j + 0], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                             pack_bf16(v[8 * j + 4], v[8 * j + 5]), pack_bf16(v[8 * j + 6], v[8 * j + 7]));
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int rr = 8 * k + (lane >> 2), cc = lane & 3;
+        const uint4 val = *reinterpret_cast<const uint4 *>(stg + rr * kStageRow + cc * 16);
+        *reinterpret_cast<uint4 *>(g.out_bf + (size_t)(row0 + rr) * g.ld_bf + q + 8 * cc) = val;
+    }
+    __syncwarp();
+}
+
+// Output-layer epilogue (bias, FP32 y only): the same staging, one 16-column half of the
+// chunk at a time (64 bytes of a row each)
+__device__ __forceinline__ void epi_out_staged(const GemmArgs &g, const uint32_t (&r)[32], int row0, int lane,
+                                               int q, const float *bias, uint8_t *stg)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 *srow = reinterpret_cast<uint4 *>(stg + lane * kStageRow);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 16 * h + 4 * j;
+            const float4 b4 = *reinterpret_cast<const float4 *>(bias + q + c);
+            srow[j] = make_uint4(__float_as_uint(__uint_as_float(r[c]) + b4.x),
+                                 __float_as_uint(__uint_as_float(r[c + 1]) + b4.y),
+                                 __float_as_uint(__uint_as_float(r[c + 2]) + b4.z),
+                                 __float_as_uint(__uint_as_float(r[c + 3]) + b4.w));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rr = 8 * k + (lane >> 2), cc = lane & 3;
+            const uint4 val = *reinterpret_cast<const uint4 *>(stg + rr * kStageRow + cc * 16);
+            *reinterpret_cast<uint4 *>(g.out_f32 + (size_t)(row0 + rr) * g.ld_f32 + q + 16 * h + 4 * cc) = val;
+        }
+        __syncwarp();
     }
 }
 
@@ -420,7 +510,11 @@ struct PersistSmem {
     static constexpr int NBAR = 2 * ST + 5;     // full, empty, tmem_full[2], tmem_empty[2], drain
     // bias of all Q <= 512 columns, read as float4: 16-byte (here 128-byte) aligned
     static constexpr int BIAS_OFF = (BAR_OFF + 8 * NBAR + 64 + 127) / 128 * 128;
-    static constexpr int BYTES = BIAS_OFF + 4 * 512 + 1024;
+    // per epilogue warp: 32 rows of staged BF16 output (epi_hidden_staged)
+    static constexpr int STG_OFF = BIAS_OFF + 4 * 512;
+    static constexpr int BYTES = STG_OFF + kEpiWarps * 32 * kStageRow + 1024;
+    static_assert(STG_OFF % 16 == 0, "16-byte staging writes");
+    static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
     static_assert(BIAS_OFF % 16 == 0, "float4 reads of the staged bias");
     static constexpr uint32_t TMEM_COLS = 2 * NT;
     static_assert(2 * NT <= 512, "two accumulators must fit the 512 TMEM columns");
@@ -549,6 +643,9 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
         // the layer's bias, once per CTA, for every tile's epilogue (named barrier 1: the
         // epilogue warps only)
         float *sbias = reinterpret_cast<float *>(sm + S::BIAS_OFF);
+        uint8_t *stg = sm + S::STG_OFF + (warp - 2) * 32 * kStageRow;
+        const bool staged = g.mode == MODE_HIDDEN && g.out_bf && !g.out_f32 && !g.out_t && g.bias;
+        const bool staged_out = g.mode == MODE_OUT && g.out_f32 && g.bias && (g.ld_f32 & 3) == 0;
         if (g.bias)
             for (int c = threadIdx.x - 64; c < g.Q; c += 32 * kEpiWarps) sbias[c] = __ldg(g.bias + c);
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
@@ -564,10 +661,23 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
             const int p0 = (t / ntn) * kBM, q0 = (t % ntn) * NT;
             const int row = p0 + 32 * qtr + lane;
             const uint32_t tl = tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(b * NT);
-            for (int c0 = half * NCOL; c0 < (half + 1) * NCOL; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tl + c0, r);
-                epi_chunk(g, r, row, q0 + c0, sbias);
+            // the next 32 columns load from TMEM while this chunk's epilogue runs
+            static_assert(NCOL % 64 == 0, "chunks are processed in pairs");
+            uint32_t ra[32], rb[32];
+            const int cb = half * NCOL;
+            tmem_ld32_async(tl + cb, ra);
+            tmem_wait32(ra);
+            for (int c0 = cb; c0 < cb + NCOL; c0 += 64) {
+                tmem_ld32_async(tl + c0 + 32, rb);
+                if (staged) epi_hidden_staged(g, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
+                else if (staged_out) epi_out_staged(g, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
+                else epi_chunk(g, ra, row, q0 + c0, sbias);
+                tmem_wait32(rb);
+                if (c0 + 64 < cb + NCOL) tmem_ld32_async(tl + c0 + 64, ra);
+                if (staged) epi_hidden_staged(g, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
+                else if (staged_out) epi_out_staged(g, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
+                else epi_chunk(g, rb, row, q0 + c0 + 32, sbias);
+                if (c0 + 64 < cb + NCOL) tmem_wait32(ra);
             }
             // this warp's reads of accumulator b are complete: release it to the MMA warp
             tc_fence_before();
