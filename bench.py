@@ -128,9 +128,14 @@ def cpu_oracle_sample(target_s: float = 15.0):
     yee.run(p, nsteps=steps2, threads=threads)
     el2 = time.perf_counter() - t
     rate = p.cells * steps2 / el2 / 1e9
+    # the same slice on one thread, two steps
+    t = time.perf_counter()
+    yee.run(p, nsteps=2, threads=1)
+    rate1 = p.cells * 2 / (time.perf_counter() - t) / 1e9
     desc = (f"FP64 oracle, {p.nx}x{p.ny}x{p.nz} slice of the lossy-line stack, {steps2} steps "
-            f"(includes its set-up), OpenMP over k-planes")
-    return rate, threads, desc
+            f"(includes its set-up), OpenMP over k-planes; single thread {rate1:.4f} Gcell/s "
+            f"(2 steps)")
+    return rate, threads, desc, rate1
 
 
 def run_reference(args, rank, world):
@@ -384,8 +389,9 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, threads, desc = cpu_oracle_sample()
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        r, threads, desc, r1 = cpu_oracle_sample()
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "single_thread_value": r1}
 
     if rank == 0:
         line = {
