@@ -149,7 +149,7 @@ def run_reference(args, rank, world):
     rates = []
     threads, desc = os.cpu_count() or 1, ""
     for _ in range(args.steps):
-        r, threads, desc = cpu_oracle_sample(target_s=per_sample)
+        r, threads, desc, _ = cpu_oracle_sample(target_s=per_sample)
         rates.append(r)
     value = float(np.median(rates))
     p = workload()
