@@ -171,11 +171,14 @@ yf_status encode_maps(yf_grid *g)
     const cuuint64_t gstr[3] = {(cuuint64_t)g->px * esz, (cuuint64_t)g->plane * esz,
                                 (cuuint64_t)g->npts * esz};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)(g->tile_y + 2), 1, 3};
+    // 64-byte L2 promotion: a window row (160 bytes from 16 bytes before the tile) would pull
+    // three 128-byte lines from DRAM at a tile whose neighbours run in another launch (the
+    // CPML frame)
     const cuuint32_t one[4] = {1, 1, 1, 1};
     for (int b = 0; b < g->nbuf(); ++b) {
         CUresult r = encode(&g->tmF[b], esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                             4, g->buf[b], gdim, gstr, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding the field tensor map failed (%d)", (int)r);
     }
@@ -184,7 +187,7 @@ yf_status encode_maps(yf_grid *g)
     const cuuint32_t cbox[4] = {32, (cuuint32_t)g->tile_y, 1, 3};
     CUresult r = encode(&g->tmC, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding the class tensor map failed (%d)", (int)r);
     YF_CUDA_TRY(tma_prepare());
     YF_CUDA_TRY(skew_prepare());
