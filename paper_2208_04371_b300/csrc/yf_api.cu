@@ -487,6 +487,7 @@ static yf_status capture_chunk(yf_grid *g)
 {
     cudaGraph_t graph = nullptr;
     const int key = graph_key(g), c0 = g->cur, h0 = g->hpar;
+    tb_unchain(g);
     YF_CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     if (g->variant == 4)
@@ -497,6 +498,7 @@ static yf_status capture_chunk(yf_grid *g)
     // capture only records: the state advances when the graph is launched
     g->cur = c0;
     g->hpar = h0;
+    tb_unchain(g);
     if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing step chunk"); }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&g->graph[key], graph, 0);
@@ -776,8 +778,11 @@ yf_status yf_step(yf_grid *g, long n)
             advance_chunk(g);
         }
     }
-    if (g->variant == 4)
+    if (g->variant == 4) {
+        tb_unchain(g);   // the first direct pair forks after everything queued so far
         for (; done + 2 <= n; done += 2) YF_CUDA_TRY(tb_pair(g, g->stream));
+        tb_unchain(g);
+    }
     for (; done < n; ++done) YF_CUDA_TRY(step_direct(g, g->stream));
     g->steps_done += n;
     return YF_OK;
@@ -995,6 +1000,7 @@ static yf_status profile_tb(yf_grid *g, long n, double *ms, int *nkern)
     double acc[3] = {0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (long t = 0; t < pairs && e == cudaSuccess; ++t) {
+        tb_unchain(g);   // each traced pair on its own
         e = tb_pair(g, g->stream, ev);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
         float m[5] = {0, 0, 0, 0, 0};

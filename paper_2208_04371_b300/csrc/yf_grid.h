@@ -111,6 +111,7 @@ yf_status tb_build(yf_grid *g);
 void tb_free(yf_grid *g);
 cudaError_t tb_single(yf_grid *g, cudaStream_t s);
 cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev = nullptr);
+void tb_unchain(yf_grid *g);   // the next pair forks after everything queued before it
 int tb_launches_pair(const yf_grid *g);
 int tb_launches_single(const yf_grid *g);
 template <typename T>

@@ -202,6 +202,10 @@ struct TbPlan {
     int box[6];          // bx0, bx1, by0, by1, bz0, bz1
     cudaStream_t stream;
     cudaEvent_t fork, join;
+    // recorded by a pair before its last epilogue: the next pair's box kernel waits on it (it
+    // touches none of the nodes that epilogue reads or writes); valid while `chained`
+    cudaEvent_t fork_next;
+    bool chained;
 };
 cudaError_t tb_prepare();
 cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,

@@ -443,6 +443,7 @@ void tb_free(yf_grid *g)
     cudaFree(t->args);
     cudaFree(t->maps);
     if (t->fork) cudaEventDestroy(t->fork);
+    if (t->fork_next) cudaEventDestroy(t->fork_next);
     if (t->join) cudaEventDestroy(t->join);
     if (t->stream) cudaStreamDestroy(t->stream);
     delete t;
@@ -557,6 +558,7 @@ yf_status tb_build(yf_grid *g)
         return bail(fail(YF_E_OOM, "variant 4: two-step arguments"));
     if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->fork_next, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(YF_E_CUDA, "variant 4: stream set-up"));
     cudaError_t e = tb_prepare();
@@ -568,6 +570,7 @@ yf_status tb_build(yf_grid *g)
 cudaError_t tb_single(yf_grid *g, cudaStream_t s)
 {
     TbPlan &t = *g->tb;
+    t.chained = false;
     cudaError_t e = launch_tma_plan<float>(t.full, g->tile_y, 2 * g->cur + g->hpar, g->status, s, &g->side);
     if (e != cudaSuccess) return e;
     g->cur = (g->cur + 1) % 3;
@@ -588,8 +591,11 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
     const bool box = t.count > 0;
     auto mark = [&](int q, cudaStream_t st) { return ev ? cudaEventRecord(ev[q], st) : cudaSuccess; };
     if (box) {
-        if ((e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(t.stream, t.fork, 0)) != cudaSuccess) return e;
+        // a pair that follows one in the same call waits only for the previous pair's second
+        // frame step, not for its epilogue: the box reads no node within four of the source
+        // or port planes and writes neither of the buffers that epilogue uses
+        if (!t.chained && (e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(t.stream, t.chained ? t.fork_next : t.fork, 0)) != cudaSuccess) return e;
         if ((e = mark(0, t.stream)) != cudaSuccess) return e;
         if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
         if ((e = mark(1, t.stream)) != cudaSuccess) return e;
@@ -611,8 +617,17 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
     g->cur = (r + 2) % 3;
     g->hpar = h;
     if ((e = mark(6, s)) != cudaSuccess) return e;
+    if (box) {
+        if ((e = cudaEventRecord(t.fork_next, s)) != cudaSuccess) return e;
+        t.chained = true;
+    }
     if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
     return mark(7, s);
+}
+
+void tb_unchain(yf_grid *g)
+{
+    if (g->tb) g->tb->chained = false;
 }
 
 int tb_launches_pair(const yf_grid *g)
