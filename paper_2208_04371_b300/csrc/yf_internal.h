@@ -183,6 +183,10 @@ void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, co
 // two-step update of the inner box (yf_tb.cu, FP32): A = the buffer at step n (read through
 // the tensor maps), C receives E^{n+2}, H^{n+3/2} on the box, B the box's outer node layer at
 // E^{n+1}, H^{n+1/2}.  The box [bx0, bx1] x [by0, by1] x [bz0, bz1] is a union of 32 x 8 tiles.
+// tile and TMA boxes of the two-step kernel
+constexpr int kTbTileX = 32, kTbTileY = 8;   // output tile
+constexpr int kTbWinX = 40, kTbWinY = 12;    // E and H windows: x from i0-4, y from j0-2
+constexpr int kTbClsX = 64, kTbClsY = 10;    // class tiles: x from i0-16, y from j0-1
 struct TbArgs {
     int px;
     long plane, npts;

@@ -18,6 +18,8 @@
 // slots (S4 reads the classes of plane q-3); H^{n+1/2} and E^{n+1} are kept for three planes,
 // H^{n+3/2} for two.
 //
+// The host side (box, work items, arguments, the pair of steps) is in yf_tb_plan.cu.
+//
 // The single-step frame advances the rest of the grid n -> n+1 (A -> B) and n+1 -> n+2
 // (B -> C).  Its second step reads the box's outermost node layer at n + 1 from B (a window
 // reaches one node into the box), so this kernel also writes E^{n+1} and H^{n+1/2} of that
@@ -27,19 +29,15 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
-#include <algorithm>
-#include <vector>
-
-#include "yf_grid.h"
 #include "yf_internal.h"
 
 namespace yf {
 namespace {
 
-constexpr int TBX = 32, TBY = 8;                     // output tile
+constexpr int TBX = kTbTileX, TBY = kTbTileY;         // output tile
 constexpr int NWARP = 12, TBN = 32 * NWARP;          // block
-constexpr int WXN = 40, WYN = 12, WN = WXN * WYN;    // windows: x from i0-4, y from j0-2
-constexpr int CXN = 64, CYN = 10, CN = CXN * CYN;    // class tile: x from i0-16, y from j0-1
+constexpr int WXN = kTbWinX, WYN = kTbWinY, WN = WXN * WYN;   // windows: x from i0-4, y from j0-2
+constexpr int CXN = kTbClsX, CYN = kTbClsY, CN = CXN * CYN;   // class tile: x from i0-16, y from j0-1
 constexpr int FST = 4, CSL = 6;                      // field stages, class slots
 constexpr int PL = 3 * WN * 4;                       // one plane of three components (bytes)
 constexpr int C_OFF = FST * 2 * PL;                  // stage s: E at s * 2PL, H at s * 2PL + PL
@@ -340,81 +338,6 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     }
 }
 
-
-PFN_cuTensorMapEncodeTiled_v12000 encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-// The box.  A two-step block over tile (i0, j0) and planes kb..ke reads step-n nodes
-// i in [i0-2, i0+33], j in [j0-2, j0+9], k in [kb-2, ke+2] and recomputes H and E on most of
-// them; all of these must see the plain update only.  So the box keeps three nodes from every
-// absorbing slab and domain wall on the low sides and two (x, y) or three (z) on the high
-// sides, and tiles whose x range widened by four nodes holds the source plane or a port plane
-// are left out (the port epilogue reads and the source writes the frame's fields between
-// the two steps).  x: the longest run of admissible 32-node tile columns; y: rows aligned to
-// the frame's tile height; z: every admissible plane.  Returns false when no box fits.
-bool choose_box(const yf_grid *g, int box[6])
-{
-    const int n = g->pml_n;
-    const int XL = g->pml_lo[0] ? n : 0, XH = g->pml_hi[0] ? g->nx - n : g->nx;
-    const int YL = g->pml_lo[1] ? n : 0, YH = g->pml_hi[1] ? g->ny - n : g->ny;
-    const int ZL = g->pml_lo[2] ? n : 0, ZH = g->pml_hi[2] ? g->nz - n : g->nz;
-    std::vector<int> special;
-    if (g->has_src) special.push_back(g->src_plane);
-    for (const PortDev &d : g->ports) special.push_back(d.plane);
-    const int ntx = g->nx / 32;
-    int best = 0, bt0 = 0, run = 0;
-    for (int tx = 0; tx < ntx; ++tx) {
-        const int i0 = 32 * tx;
-        bool ok = i0 - 3 >= XL && i0 + 34 <= XH;
-        for (int s : special) ok = ok && !(s >= i0 - 4 && s <= i0 + 35);
-        run = ok ? run + 1 : 0;
-        if (run > best) { best = run; bt0 = tx - run + 1; }
-    }
-    const int A = std::max(8, g->tile_y);
-    const int by0 = (YL + 3 + A - 1) / A * A, byE = (YH - 2) / A * A;
-    const int bz0 = ZL + 3, bz1 = ZH - 3;
-    if (best < 1 || byE <= by0 || bz1 - bz0 + 1 < 4) return false;
-    box[0] = 32 * bt0;
-    box[1] = 32 * (bt0 + best) - 1;
-    box[2] = by0;
-    box[3] = byE - 1;
-    box[4] = bz0;
-    box[5] = bz1;
-    return true;
-}
-
-yf_status upload_items(const std::vector<BatchItem> items[5], TmaPlan *pl)
-{
-    std::vector<BatchItem> all;
-    for (int k = 0; k < 5; ++k) {
-        pl->offset[k] = (int)all.size();
-        pl->count[k] = (int)items[k].size();
-        all.insert(all.end(), items[k].begin(), items[k].end());
-    }
-    YF_CUDA_TRY(cudaMalloc(&pl->items, std::max<size_t>(1, all.size()) * sizeof(BatchItem)));
-    if (!all.empty())
-        YF_CUDA_TRY(cudaMemcpy(pl->items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
-    return YF_OK;
-}
-
-int kinds_used(const TmaPlan &pl)
-{
-    int k = 0;
-    for (int q = 0; q < 5; ++q) k += pl.count[q] > 0;
-    return k;
-}
-
 }  // namespace
 
 cudaError_t tb_prepare()
@@ -429,212 +352,5 @@ cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, co
     k_yee_tb2<<<count, TBN, TB_BYTES, s>>>(items, args, maps, phase, status);
     return cudaGetLastError();
 }
-
-void tb_free(yf_grid *g)
-{
-    TbPlan *t = g->tb;
-    if (!t) return;
-    if (t->stream) cudaStreamSynchronize(t->stream);
-    cudaFree(t->full.items);
-    cudaFree(t->full.args);
-    cudaFree(t->full.maps);
-    cudaFree(t->frame.items);
-    cudaFree(t->items);
-    cudaFree(t->args);
-    cudaFree(t->maps);
-    if (t->fork) cudaEventDestroy(t->fork);
-    if (t->fork_next) cudaEventDestroy(t->fork_next);
-    if (t->join) cudaEventDestroy(t->join);
-    if (t->stream) cudaStreamDestroy(t->stream);
-    delete t;
-    g->tb = nullptr;
-}
-
-// Plan of variant 4 on a finalised FP32 grid whose three field buffers exist and whose field
-// maps (tmF[0..2], tmC) are encoded for the grid's tile height.
-yf_status tb_build(yf_grid *g)
-{
-    if (g->tb) return YF_OK;
-    if (g->prec != YF_FP32) return fail(YF_E_INVALID, "variant 4 needs FP32 fields");
-    if (!g->buf[2]) return fail(YF_E_STATE, "variant 4: third field buffer missing");
-    // the two-step kernel indexes a buffer's six components with 32-bit offsets
-    if (6 * g->npts > 2147483647L)
-        return fail(YF_E_INVALID, "variant 4 needs 6 (nz+1)(ny+1) px < 2^31 (grid has %ld points)", g->npts);
-    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
-    if (!encode) return fail(YF_E_CUDA, "cuTensorMapEncodeTiled is not available");
-    TbPlan *t = new TbPlan();
-    g->tb = t;
-    auto bail = [&](yf_status st) { tb_free(g); return st; };
-
-    std::vector<BatchItem> full[5], frame[5], two;
-    tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full);
-    const bool have_box = choose_box(g, t->box);
-    const int *B = t->box;
-    for (int k = 0; k < 5; ++k)
-        for (const BatchItem &it : full[k]) {
-            const bool inxy = have_box && it.i0 >= B[0] && it.i0 <= B[1] && it.j0 >= B[2] && it.j0 <= B[3];
-            if (!inxy || it.ke < B[4] || it.kb > B[5]) {
-                frame[k].push_back(it);
-                continue;
-            }
-            if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
-            if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
-        }
-    // z-planes per two-step block: twice the one-step segment (the two-step block re-reads four
-    // halo planes instead of two), at most the one-step kernels' limit
-    const int seg = std::min(kMaxKseg, 2 * g->kseg);
-    if (have_box)
-        for (int kb = B[4]; kb <= B[5]; kb += seg)
-            for (int j0 = B[2]; j0 <= B[3]; j0 += TBY)
-                for (int i0 = B[0]; i0 <= B[1]; i0 += TBX)
-                    two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + seg - 1)});
-    yf_status st;
-    if ((st = upload_items(full, &t->full)) != YF_OK) return bail(st);
-    if ((st = upload_items(frame, &t->frame)) != YF_OK) return bail(st);
-    t->count = (int)two.size();
-    if (cudaMalloc(&t->items, std::max<size_t>(1, two.size()) * sizeof(BatchItem)) != cudaSuccess ||
-        (!two.empty() && cudaMemcpy(t->items, two.data(), two.size() * sizeof(BatchItem),
-                                    cudaMemcpyHostToDevice) != cudaSuccess))
-        return bail(fail(YF_E_OOM, "variant 4: work items"));
-
-    // single-step arguments by slot 2 * src + hpar (B = the next buffer), shared by both plans
-    std::vector<FusedArgs<float>> fa(6);
-    std::vector<CUtensorMap> fm(12);
-    const int c0 = g->cur, h0 = g->hpar;
-    for (int r = 0; r < 3; ++r)
-        for (int h = 0; h < 2; ++h) {
-            g->cur = r;
-            g->hpar = h;
-            fa[2 * r + h] = fused_args<float>(g);
-            fm[2 * (2 * r + h)] = g->tmF[r];
-            fm[2 * (2 * r + h) + 1] = g->tmC;
-        }
-    g->cur = c0;
-    g->hpar = h0;
-    if (cudaMalloc(&t->full.args, fa.size() * sizeof(FusedArgs<float>)) != cudaSuccess ||
-        cudaMemcpy(t->full.args, fa.data(), fa.size() * sizeof(FusedArgs<float>), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMalloc(&t->full.maps, fm.size() * sizeof(CUtensorMap)) != cudaSuccess ||
-        cudaMemcpy(t->full.maps, fm.data(), fm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(YF_E_OOM, "variant 4: step arguments"));
-    t->frame.args = t->full.args;
-    t->frame.maps = t->full.maps;
-
-    // two-step arguments and maps by source buffer r: B = buf[r+1], C = buf[r+2]
-    TbArgs ta[3];
-    CUtensorMap tm[6];
-    const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
-    const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
-    const cuuint32_t wbox[4] = {WXN, WYN, 1, 3};
-    const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
-    const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
-    const cuuint32_t cbox[4] = {CXN, CYN, 1, 3};
-    const cuuint32_t one[4] = {1, 1, 1, 1};
-    for (int r = 0; r < 3; ++r) {
-        TbArgs &a = ta[r];
-        a.px = g->px;
-        a.plane = g->plane;
-        a.npts = g->npts;
-        a.rdx = (float)(1.0 / g->dx);
-        a.rdy = (float)(1.0 / g->dy);
-        a.rdz = (float)(1.0 / g->dz);
-        a.db = (float)(g->dt / kMu0);
-        a.ctab = (const float *)g->ctab;
-        a.B = (float *)g->buf[(r + 1) % 3];
-        a.C = (float *)g->buf[(r + 2) % 3];
-        a.bx0 = B[0]; a.bx1 = B[1]; a.by0 = B[2]; a.by1 = B[3]; a.bz0 = B[4]; a.bz1 = B[5];
-        CUresult cr = encode(&tm[2 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr == CUDA_SUCCESS)
-            cr = encode(&tm[2 * r + 1], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr != CUDA_SUCCESS) return bail(fail(YF_E_CUDA, "variant 4: tensor map encoding failed (%d)", (int)cr));
-    }
-    if (cudaMalloc(&t->args, sizeof(ta)) != cudaSuccess ||
-        cudaMemcpy(t->args, ta, sizeof(ta), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMalloc(&t->maps, sizeof(tm)) != cudaSuccess ||
-        cudaMemcpy(t->maps, tm, sizeof(tm), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(YF_E_OOM, "variant 4: two-step arguments"));
-    if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->fork_next, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess)
-        return bail(fail(YF_E_CUDA, "variant 4: stream set-up"));
-    cudaError_t e = tb_prepare();
-    if (e != cudaSuccess) return bail(cuda_fail(e, "variant 4: shared-memory opt-in"));
-    return YF_OK;
-}
-
-// one time step over the whole grid (stencil only; the caller adds the epilogue)
-cudaError_t tb_single(yf_grid *g, cudaStream_t s)
-{
-    TbPlan &t = *g->tb;
-    t.chained = false;
-    cudaError_t e = launch_tma_plan<float>(t.full, g->tile_y, 2 * g->cur + g->hpar, g->status, s, &g->side);
-    if (e != cudaSuccess) return e;
-    g->cur = (g->cur + 1) % 3;
-    g->hpar ^= 1;
-    return cudaSuccess;
-}
-
-// two time steps with both epilogues: the box n -> n+2 on a side stream, concurrently the
-// frame n -> n+1 and its epilogue; then, once the box is done, the frame n+1 -> n+2 and its
-// epilogue
-// ev (tracing, may be null): 8 events recorded around the box kernel on its stream (0, 1) and
-// around each frame step and epilogue on s (2..4 first step, 5..7 second)
-cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
-{
-    TbPlan &t = *g->tb;
-    const int r = g->cur, h = g->hpar, r1 = (r + 1) % 3;
-    cudaError_t e;
-    const bool box = t.count > 0;
-    auto mark = [&](int q, cudaStream_t st) { return ev ? cudaEventRecord(ev[q], st) : cudaSuccess; };
-    if (box) {
-        // a pair that follows one in the same call waits only for the previous pair's second
-        // frame step, not for its epilogue: the box reads no node within four of the source
-        // or port planes and writes neither of the buffers that epilogue uses
-        if (!t.chained && (e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(t.stream, t.chained ? t.fork_next : t.fork, 0)) != cudaSuccess) return e;
-        if ((e = mark(0, t.stream)) != cudaSuccess) return e;
-        if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
-        if ((e = mark(1, t.stream)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(t.join, t.stream)) != cudaSuccess) return e;
-    } else if (ev) {
-        if ((e = mark(0, s)) != cudaSuccess || (e = mark(1, s)) != cudaSuccess) return e;
-    }
-    if ((e = mark(2, s)) != cudaSuccess) return e;
-    if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r + h, g->status, s, &g->side)) != cudaSuccess) return e;
-    g->cur = r1;
-    g->hpar = h ^ 1;
-    if ((e = mark(3, s)) != cudaSuccess) return e;
-    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
-    if ((e = mark(4, s)) != cudaSuccess) return e;
-    if (box && (e = cudaStreamWaitEvent(s, t.join, 0)) != cudaSuccess) return e;
-    if ((e = mark(5, s)) != cudaSuccess) return e;
-    if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r1 + (h ^ 1), g->status, s, &g->side)) != cudaSuccess)
-        return e;
-    g->cur = (r + 2) % 3;
-    g->hpar = h;
-    if ((e = mark(6, s)) != cudaSuccess) return e;
-    if (box) {
-        if ((e = cudaEventRecord(t.fork_next, s)) != cudaSuccess) return e;
-        t.chained = true;
-    }
-    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
-    return mark(7, s);
-}
-
-void tb_unchain(yf_grid *g)
-{
-    if (g->tb) g->tb->chained = false;
-}
-
-int tb_launches_pair(const yf_grid *g)
-{
-    return 2 * kinds_used(g->tb->frame) + (g->tb->count > 0) + 2;
-}
-
-int tb_launches_single(const yf_grid *g) { return kinds_used(g->tb->full) + 1; }
 
 }  // namespace yf
