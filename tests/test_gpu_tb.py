@@ -68,9 +68,14 @@ def test_box_is_the_documented_one(gpu):
         assert gpu.tb_box(g.h) == (96, 159, 16, 55, 3, 39)
 
 
-def test_variant4_matches_oracle(gpu, tb_ref):
+@pytest.mark.parametrize("tile_y,kseg", [(8, 16), (4, 5), (16, 7), (8, 1), (8, 32)])
+def test_variant4_matches_oracle(gpu, tb_ref, tile_y, kseg):
+    """Frame tile heights 4, 8, 16 (the box rows align to max(8, tile_y)) and box segments of
+    2, 10, 14, 32 and 64 planes (2 kseg, at most 64)."""
     p, ref = tb_ref
-    with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
+    with gpu.Grid(p, prec=gpu.FP32, variant=4, tile_y=tile_y, kseg=kseg) as g:
+        box = gpu.tb_box(g.h)
+        assert box is not None and (box[2] % max(8, tile_y)) == 0 and (box[3] + 1) % max(8, tile_y) == 0
         g.step(61)
         g.sync()
         f = g.fields()
