@@ -182,7 +182,9 @@ yf_status yf_tb_box(yf_grid *g, int box[6]);
  * the fastest, resets fields, auxiliaries, spectra and the step count to zero, and caches the
  * choice in the JSON file cache_path (NULL: no cache) under a key of precision, size bucket
  * (cells rounded up to a power of two) and presence of absorbing slabs; a cached key skips
- * the timing.  The chosen tile_y and kseg are returned (either pointer may be NULL). */
+ * the timing.  The chosen tile_y and kseg are returned (either pointer may be NULL), and the
+ * grid is left on variant 2 with them (set variant 4 again afterwards to use the two-step
+ * path with the chosen tile). */
 yf_status yf_autotune(yf_grid *g, const char *cache_path, int reps, int *tile_y, int *kseg);
 
 /* Advance n time steps asynchronously on the handle's stream (Sec. II-A time loop:
