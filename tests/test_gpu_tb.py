@@ -203,3 +203,25 @@ def test_grid_without_a_box_steps_exactly_like_variant2(gpu):
             out[v] = g.fields()
     assert np.array_equal(out[2], out[4])
 
+
+
+def test_pec_cavity_variant4_matches_variant2(gpu):
+    """A closed lossless PEC cavity (no CPML, source or ports) from seeded random fields: the
+    box then reaches three nodes from every wall.  200 steps, two-step path against one-step."""
+    nx, ny, nz = 100, 60, 40
+    p = W.Problem(nx=nx, ny=ny, nz=nz, dx=1e-3, dy=0.8e-3, dz=1.1e-3, courant=0.95,
+                  ids=np.zeros((nz, ny, nx), np.uint8), eps_r=np.array([1.0]),
+                  sigma=np.array([0.0]), mu_r=np.array([1.0]), is_pec=np.array([0], np.uint8),
+                  bc=(0,) * 6, pml_cells=0)
+    f0 = W.uniform_array(0xCAB, 6 * (nz + 1) * (ny + 1) * (nx + 1), -1.0, 1.0).reshape(
+        6, nz + 1, ny + 1, nx + 1)
+    out = {}
+    for v in (2, 4):
+        with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
+            if v == 4:
+                assert gpu.tb_box(g.h) == (32, 95, 8, 55, 3, 37)
+            g.set_fields(f0)
+            g.step(200)
+            g.sync()
+            out[v] = g.fields()
+    assert rel_l2(out[4], out[2]) <= 1e-5
