@@ -1,30 +1,31 @@
 // Two-step (temporally blocked) Yee update of the inner box, FP32 (variant 4).
 //
-// The inner box is a set of whole 32 x 8 tiles and a z range that stay at least two nodes
-// away from every CPML slab, domain wall, source plane and port plane, so only the plain
-// Yee update (materials through the class table) happens in and around it.  One block takes
-// one tile over a z segment [kb, ke] and advances it from step n (buffer A) to step n + 2
-// (buffer C) in one pass over HBM:
+// The inner box is a set of whole 32 x 8 tiles and a z range that keep at least three nodes
+// from every CPML slab and domain wall and four from the source and port planes, so only the
+// plain Yee update (materials through the class table) happens in and around it.  One block
+// takes one tile over a z segment [kb, ke] and advances it from step n (buffer A) to step
+// n + 2 (buffer C) in one pass over HBM:
 //   S1  H^{n+1/2}  on the tile grown by 2 nodes on the low sides, 1 on the high sides
 //   S2  E^{n+1}    on the tile grown by 1 node on every side
 //   S3  H^{n+3/2}  on the tile grown by 1 node on the low sides
 //   S4  E^{n+2}    on the tile, written to C together with H^{n+3/2}
-// (the far corner of the S1 and S2 regions feeds nothing and is skipped).  The grown rings
-// recompute what neighbouring blocks (or the single-step frame) own, from the same step-n data.
-// z is marched with the stages skewed so that each plane iteration q has two phases separated
-// by one block barrier: {S1 on plane q-1, S3 on plane q-3}, then {S2 on plane q-1, S4 on plane
-// q-3}; every input of a phase comes from an earlier phase.  Step-n planes arrive by TMA two planes ahead: E and H windows of
-// 40 x 12 nodes (x from i0-4, y from j0-2) in four stages, the class tiles (64 x 10) in six
-// slots (S4 reads the classes of plane q-3); H^{n+1/2} and E^{n+1} are kept for three planes,
-// H^{n+3/2} for two.
+// The grown rings recompute, from the same step-n data, what neighbouring blocks (or the
+// single-step frame) own.  Threads work on x-pairs of nodes, so some regions reach one node
+// further; those extra nodes feed nothing.
 //
-// The host side (box, work items, arguments, the pair of steps) is in yf_tb_plan.cu.
+// z is marched with the stages skewed so that each plane iteration q has two phases separated
+// by one block barrier: {S1 on plane q-1, S3 on plane q-3}, then {S2 on plane q-1, S4 on
+// plane q-3}; every input of a phase comes from an earlier phase.  Step-n planes arrive by TMA
+// two planes ahead: E and H windows of 40 x 12 nodes (x from i0-4, y from j0-2) in four
+// stages, the class tiles (64 x 10) in six slots (S4 reads the classes of plane q-3).
+// H^{n+1/2} and E^{n+1} are kept for three planes, H^{n+3/2} for two.
 //
 // The single-step frame advances the rest of the grid n -> n+1 (A -> B) and n+1 -> n+2
 // (B -> C).  Its second step reads the box's outermost node layer at n + 1 from B (a window
 // reaches one node into the box), so this kernel also writes E^{n+1} and H^{n+1/2} of that
 // layer into B.  Every mbarrier wait is bounded; a wait that gives up sets bit 1 of the status
-// word and the block returns.
+// word and the block returns.  The host side (box, work items, arguments, the pair of steps)
+// is in yf_tb_plan.cu.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
