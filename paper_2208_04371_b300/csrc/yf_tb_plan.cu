@@ -29,8 +29,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
 }
 
 // The box.  A two-step block over tile (i0, j0) and planes kb..ke reads step-n nodes
-// i in [i0-2, i0+33], j in [j0-2, j0+9], k in [kb-2, ke+2] and recomputes H and E on most of
-// them; all of these must see the plain update only.  So the box keeps three nodes from every
+// i in [i0-2, i0+34], j in [j0-2, j0+9], k in [kb-2, ke+2] and recomputes H and E on most of
+// them (the values at i0+33 and i0+34 only feed nodes nobody uses); the nodes it needs must
+// see the plain update only.  So the box keeps three nodes from every
 // absorbing slab and domain wall on the low sides and two (x, y) or three (z) on the high
 // sides, and tiles whose x range widened by four nodes holds the source plane or a port plane
 // are left out (the port epilogue reads and the source writes the frame's fields between
