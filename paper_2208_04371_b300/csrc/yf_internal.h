@@ -178,8 +178,9 @@ struct TmaPlan {
 template <typename T>
 cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *status, cudaStream_t s,
                             const SideStream *side);
+// mixed_seg > 0: the all-CPML kind (4) in segments of at most mixed_seg planes
 void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
-               const int hi[3], std::vector<BatchItem> items[5]);
+               const int hi[3], std::vector<BatchItem> items[5], int mixed_seg = 0);
 // two-step update of the inner box (yf_tb.cu, FP32): A = the buffer at step n (read through
 // the tensor maps), C receives E^{n+2}, H^{n+3/2} on the box, B the box's outer node layer at
 // E^{n+1}, H^{n+1/2}.  The box [bx0, bx1] x [by0, by1] x [bz0, bz1] is a union of 32 x 8 tiles.

@@ -128,7 +128,7 @@ yf_status tb_build(yf_grid *g)
     auto bail = [&](yf_status st) { tb_free(g); return st; };
 
     std::vector<BatchItem> full[5], frame[5], two;
-    tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full);
+    tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full, 8);
     const bool have_box = choose_box(g, t->box);
     const int *B = t->box;
     for (int k = 0; k < 5; ++k)

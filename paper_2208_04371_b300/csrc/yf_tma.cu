@@ -647,10 +647,8 @@ cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *stat
 // nodes avoid the x and y slabs, planes from the warm-up plane on outside the z slabs) is kind
 // 0; tiles outside it in x only -> kind 1 (x CPML), in y only -> kind 2, in z only -> kind 3
 // (z CPML), anything else -> kind 4 (all CPML).  z segments never straddle the z-slab limits.
-constexpr int kMixedSeg = 8;   // z-planes per block of the all-CPML work kind
-
 void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, const int lo[3],
-               const int hi[3], std::vector<BatchItem> items[5])
+               const int hi[3], std::vector<BatchItem> items[5], int mixed_seg)
 {
     // Tiles cover node columns 0 .. nx-1 and rows 0 .. ny-1.  The last node column i = nx
     // (and row j = ny) joins a tile only when nx (ny) is not a multiple of the tile: on that
@@ -692,11 +690,11 @@ void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, co
                 if (!hp) kind = 0;
                 else if (inz) kind = inx ? (iny ? 0 : 2) : (iny ? 1 : 4);
                 else kind = (inx && iny) ? 3 : 4;
-                if (kind == 4) {
-                    // the all-CPML kind is the slowest per plane and a small grid: shorter
-                    // segments give it more blocks and a shorter longest block
-                    for (int k0 = sg.first; k0 <= sg.second; k0 += kMixedSeg)
-                        items[kind].push_back(BatchItem{inst, tx * TX, ty * TY, k0, std::min(sg.second, k0 + kMixedSeg - 1)});
+                if (kind == 4 && mixed_seg > 0) {
+                    // where the all-CPML kind is small (one large grid), shorter segments give
+                    // it more blocks and a shorter longest block
+                    for (int k0 = sg.first; k0 <= sg.second; k0 += mixed_seg)
+                        items[kind].push_back(BatchItem{inst, tx * TX, ty * TY, k0, std::min(sg.second, k0 + mixed_seg - 1)});
                     continue;
                 }
                 items[kind].push_back(BatchItem{inst, tx * TX, ty * TY, sg.first, sg.second});
