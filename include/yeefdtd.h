@@ -286,9 +286,10 @@ yf_status yf_reset(yf_grid *g);
 /* Tracing: run n steps without graphs, bracketing every kernel launch with CUDA events
  * on the handle's stream, and return the mean duration in ms per launch of each kernel
  * of a step (names via yf_kernel_name).  *nkern receives the number of kernels (<= 8).
- * Variant 4 runs max(1, n/2) pairs of steps and reports the box kernel (timed on its own
- * stream, one launch per pair), the frame step (all its work kinds, two per pair) and the
- * epilogue; the box kernel overlaps the first frame step, so its time includes that sharing. */
+ * Variant 4 runs max(1, n/2) pairs of steps and reports four entries: the box kernel (timed
+ * on its own stream, one launch per pair), the first frame step (all its work kinds; it runs
+ * beside the box kernel, so both times include that sharing), the second frame step (after
+ * the box kernel) and the epilogue (mean of the two per pair). */
 yf_status yf_profile_steps(yf_grid *g, long n, double *ms_per_launch, int *nkern);
 const char *yf_kernel_name(yf_grid *g, int idx);
 

@@ -990,14 +990,14 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
     return e;
 }
 
-// variant 4: pairs of steps; per launch the box kernel (one per pair), the frame step and the
-// epilogue (two each per pair)
+// variant 4: pairs of steps; per launch the box kernel (one per pair), the first frame step
+// (beside the box kernel), the second frame step (after it) and the epilogue (two per pair)
 static yf_status profile_tb(yf_grid *g, long n, double *ms, int *nkern)
 {
     cudaEvent_t ev[8];
     for (int q = 0; q < 8; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
     const long pairs = n < 2 ? 1 : n / 2;
-    double acc[3] = {0, 0, 0};
+    double acc[4] = {0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (long t = 0; t < pairs && e == cudaSuccess; ++t) {
         tb_unchain(g);   // each traced pair on its own
@@ -1007,14 +1007,15 @@ static yf_status profile_tb(yf_grid *g, long n, double *ms, int *nkern)
         const int from[5] = {0, 2, 3, 5, 6}, to[5] = {1, 3, 4, 6, 7};
         for (int q = 0; q < 5 && e == cudaSuccess; ++q) e = cudaEventElapsedTime(&m[q], ev[from[q]], ev[to[q]]);
         acc[0] += m[0];
-        acc[1] += 0.5 * (m[1] + m[3]);
-        acc[2] += 0.5 * (m[2] + m[4]);
+        acc[1] += m[1];
+        acc[2] += m[3];
+        acc[3] += 0.5 * (m[2] + m[4]);
     }
     for (int q = 0; q < 8; ++q) cudaEventDestroy(ev[q]);
     YF_CUDA_TRY(e);
     g->steps_done += 2 * pairs;
-    for (int q = 0; q < 3; ++q) ms[q] = acc[q] / (double)pairs;
-    *nkern = 3;
+    for (int q = 0; q < 4; ++q) ms[q] = acc[q] / (double)pairs;
+    *nkern = 4;
     return YF_OK;
 }
 
@@ -1054,9 +1055,10 @@ const char *yf_kernel_name(yf_grid *g, int idx)
     static const char *fused[] = {"k_yee_fused", "k_epilogue"};
     static const char *tma[] = {"k_yee_tma_batch", "k_epilogue"};
     static const char *skew[] = {"k_yee_skew", "k_epilogue"};
-    static const char *tb[] = {"k_yee_tb2", "k_yee_tma_batch", "k_epilogue"};
+    static const char *tb[] = {"k_yee_tb2", "k_yee_tma_batch (frame step 1)", "k_yee_tma_batch (frame step 2)",
+                               "k_epilogue"};
     if (!g) return "";
-    if (g->variant == 4) return (idx >= 0 && idx < 3) ? tb[idx] : "";
+    if (g->variant == 4) return (idx >= 0 && idx < 4) ? tb[idx] : "";
     if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
     if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
     if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";

@@ -495,10 +495,10 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 // Block b takes work item b (instance, tile origin, z-segment); the instance's arguments for
 // the current buffer parity are copied to shared memory behind the TMA layout.  FP32 kinds
 // with one row per thread are held to five resident blocks per SM (the shared-memory limit;
-// 48 registers), the mixed-slab kind to three; FP64 and two-row tiles keep the compiler's
+// 48 registers), the all-CPML kind to four (64); FP64 and two-row tiles keep the compiler's
 // choice (a cap would spill).
 template <typename T, int TX, int TYT, int CY, int PM>
-__global__ void __launch_bounds__(TX *TYT, (sizeof(T) == 4 && CY == 1) ? ((PM == 7) ? 3 : 5) : 1)
+__global__ void __launch_bounds__(TX *TYT, (sizeof(T) == 4 && CY == 1) ? ((PM == 7) ? 4 : 5) : 1)
     k_yee_tma_batch(const BatchItem *items, const FusedArgs<T> *args, const CUtensorMap *maps,
                     int parity, int *status)
 {
