@@ -156,7 +156,12 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i = i0 + tx, jb = j0 + ty * CY;
     const long plane = P.plane, npts = P.npts;
-    const int px = P.px, NX1 = P.nx + 1, NY1 = P.ny + 1;
+    // arguments the plane loop uses, held in registers (the shared copy would be re-read after
+    // every barrier)
+    const T rdx = P.rdx, rdy = P.rdy, rdz = P.rdz, db = P.db;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    T *const Bo = P.B;
+    const int px = P.px, NX1 = nx + 1, NY1 = ny + 1;
     const int n = P.n, L = P.L;
 
     // TMA writes need 128-byte aligned shared destinations
@@ -172,19 +177,19 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
     if (HPX) {
         for (int q = tid; q < 6 * BX; q += NT) {
             const int k = q / BX, gi = i0 - XO + q % BX;
-            PX[q] = (P.prof[0] && gi >= 0 && gi <= P.nx) ? P.prof[0][k * NX1 + gi] : (T)0;
+            PX[q] = (P.prof[0] && gi >= 0 && gi <= nx) ? P.prof[0][k * NX1 + gi] : (T)0;
         }
     }
     if (HPY) {
         for (int q = tid; q < 6 * WY; q += NT) {
             const int k = q / WY, gj = j0 - 1 + q % WY;
-            PY[q] = (P.prof[1] && gj >= 0 && gj <= P.ny) ? P.prof[1][k * NY1 + gj] : (T)0;
+            PY[q] = (P.prof[1] && gj >= 0 && gj <= ny) ? P.prof[1][k * NY1 + gj] : (T)0;
         }
     }
     if (HPZ) {
         for (int q = tid; q < 6 * ZMAX; q += NT) {
             const int k = q / ZMAX, gp = kb - 1 + q % ZMAX;
-            PZ[q] = (P.prof[2] && gp >= 0 && gp <= P.nz) ? P.prof[2][k * (P.nz + 1) + gp] : (T)0;
+            PZ[q] = (P.prof[2] && gp >= 0 && gp <= nz) ? P.prof[2][k * (nz + 1) + gp] : (T)0;
         }
     }
     __syncthreads();
@@ -219,15 +224,15 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
     }
 
     // per-thread constants
-    const bool col_live = i <= P.nx;
-    const int sx = HPX ? slab_i(i, P.nx, n, P.lo[0], P.hi[0]) : -1;
+    const bool col_live = i <= nx;
+    const int sx = HPX ? slab_i(i, nx, n, P.lo[0], P.hi[0]) : -1;
     const int lx = tx + XO;            // staged x-profile index of the own column
     int sy[CY];
     bool rlive[CY];
 #pragma unroll
     for (int r = 0; r < CY; ++r) {
-        sy[r] = HPY ? slab_i(jb + r, P.ny, n, P.lo[1], P.hi[1]) : -1;
-        rlive[r] = col_live && jb + r <= P.ny;
+        sy[r] = HPY ? slab_i(jb + r, ny, n, P.lo[1], P.hi[1]) : -1;
+        rlive[r] = col_live && jb + r <= ny;
     }
     const int w0 = (ty * CY + 1) * BX + (tx + XO);   // window index of row r: w0 + r * BX
 
@@ -247,7 +252,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
             h_j = j0 - 1;
             h_lx = e + XO;
             h_ly = 0;
-            h_live = j0 > 0 && h_i <= P.nx;
+            h_live = j0 > 0 && h_i <= nx;
         } else {
             const int e = tid - 2 * TX;
             const int r = e < TY ? e : e - TY;
@@ -257,10 +262,10 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
             h_j = j0 + r;
             h_lx = XO - 1;
             h_ly = r + 1;
-            h_live = i0 > 0 && h_j <= P.ny;
+            h_live = i0 > 0 && h_j <= ny;
         }
-        if (HPX && h_live) h_sx = slab_i(h_i, P.nx, n, P.lo[0], P.hi[0]);
-        if (HPY && h_live) h_sy = slab_i(h_j, P.ny, n, P.lo[1], P.hi[1]);
+        if (HPX && h_live) h_sx = slab_i(h_i, nx, n, P.lo[0], P.hi[0]);
+        if (HPY && h_live) h_sy = slab_i(h_j, ny, n, P.lo[1], P.hi[1]);
     }
 
     // CPML auxiliaries of plane q for the own rows (pv) and the halo value (hv):
@@ -272,8 +277,8 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
     T pv[CY][12];
     T hv[2] = {0, 0};
     auto fetch = [&](int q) {
-        if (!HP || q < 0 || q > P.nz) return;
-        const int szq = HPZ ? slab_i(q, P.nz, n, P.lo[2], P.hi[2]) : -1;
+        if (!HP || q < 0 || q > nz) return;
+        const int szq = HPZ ? slab_i(q, nz, n, P.lo[2], P.hi[2]) : -1;
 #pragma unroll
         for (int r = 0; r < CY; ++r) {
             const int j = jb + r;
@@ -334,7 +339,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
         const uint8_t *cl = stp + 2 * Lay::WIN_PAD;
         const T *ex1 = reinterpret_cast<const T *>(stn), *ey1 = ex1 + WN;
         const bool pin = p >= 0;
-        const int sz = (HPZ && pin) ? slab_i(p, P.nz, n, P.lo[2], P.hi[2]) : -1;
+        const int sz = (HPZ && pin) ? slab_i(p, nz, n, P.lo[2], P.hi[2]) : -1;
         const int lz = p - kb + 1;   // staged z-profile index of plane p
 
         // E^n of this thread's rows (plus the row above for the y differences)
@@ -356,19 +361,19 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 
         if (p < kb) {
             // warm-up plane kb - 1: own H_x, H_y (the E update of plane kb needs them)
-            if (pin && p < P.nz) {
+            if (pin && p < nz) {
 #pragma unroll
                 for (int r = 0; r < CY; ++r) {
                     const int w = w0 + r * BX, ly = ty * CY + r + 1;
-                    T d1 = (ezv[r + 1] - ezv[r]) * P.rdy, d2 = (ey1v[r] - eyv[r]) * P.rdz;
+                    T d1 = (ezv[r + 1] - ezv[r]) * rdy, d2 = (ey1v[r] - eyv[r]) * rdz;
                     if (HPY && sy[r] >= 0) d1 = cpt(d1, pv[r][0], (T *)nullptr, PY, WY, 3, ly);
                     if (HPZ && sz >= 0) d2 = cpt(d2, pv[r][4], (T *)nullptr, PZ, ZMAX, 3, lz);
-                    hx_prev[r] = hox[w] - P.db * (d1 - d2);
-                    d1 = (ex1v[r] - exv[r]) * P.rdz;
-                    d2 = (ezx[r] - ezv[r]) * P.rdx;
+                    hx_prev[r] = hox[w] - db * (d1 - d2);
+                    d1 = (ex1v[r] - exv[r]) * rdz;
+                    d2 = (ezx[r] - ezv[r]) * rdx;
                     if (HPZ && sz >= 0) d1 = cpt(d1, pv[r][5], (T *)nullptr, PZ, ZMAX, 3, lz);
                     if (HPX && sx >= 0) d2 = cpt(d2, pv[r][8], (T *)nullptr, PX, BX, 3, lx);
-                    hy_prev[r] = hoy[w] - P.db * (d1 - d2);
+                    hy_prev[r] = hoy[w] - db * (d1 - d2);
                 }
             }
         } else {
@@ -377,59 +382,59 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 #pragma unroll
             for (int r = 0; r < CY; ++r) {
                 const int w = w0 + r * BX, j = jb + r, ly = ty * CY + r + 1;
-                const bool vx = rlive[r] && j < P.ny && p < P.nz;
-                const bool vy = rlive[r] && i < P.nx && p < P.nz;
-                const bool vz = rlive[r] && i < P.nx && j < P.ny;
+                const bool vx = rlive[r] && j < ny && p < nz;
+                const bool vy = rlive[r] && i < nx && p < nz;
+                const bool vz = rlive[r] && i < nx && j < ny;
                 // H_x(i, j+1/2, p+1/2) -= dt/mu0 (dEz/dy - dEy/dz)
-                T d1 = (ezv[r + 1] - ezv[r]) * P.rdy, d2 = (ey1v[r] - eyv[r]) * P.rdz;
+                T d1 = (ezv[r + 1] - ezv[r]) * rdy, d2 = (ey1v[r] - eyv[r]) * rdz;
                 if (HPY && sy[r] >= 0)
                     d1 = cpt(d1, pv[r][0], vx ? P.psiHw[1][0] + (p * L + sy[r]) * px + i : (T *)nullptr, PY, WY, 3, ly);
                 if (HPZ && sz >= 0)
                     d2 = cpt(d2, pv[r][4], vx ? P.psiHw[2][0] + (sz * NY1 + j) * px + i : (T *)nullptr, PZ, ZMAX, 3, lz);
-                hx[r] = hox[w] - P.db * (d1 - d2);
+                hx[r] = hox[w] - db * (d1 - d2);
                 // H_y(i+1/2, j, p+1/2) -= dt/mu0 (dEx/dz - dEz/dx)
-                d1 = (ex1v[r] - exv[r]) * P.rdz;
-                d2 = (ezx[r] - ezv[r]) * P.rdx;
+                d1 = (ex1v[r] - exv[r]) * rdz;
+                d2 = (ezx[r] - ezv[r]) * rdx;
                 if (HPZ && sz >= 0)
                     d1 = cpt(d1, pv[r][5], vy ? P.psiHw[2][1] + (sz * NY1 + j) * px + i : (T *)nullptr, PZ, ZMAX, 3, lz);
                 if (HPX && sx >= 0)
                     d2 = cpt(d2, pv[r][8], vy ? P.psiHw[0][0] + (p * NY1 + j) * L + sx : (T *)nullptr, PX, BX, 3, lx);
-                hy[r] = hoy[w] - P.db * (d1 - d2);
+                hy[r] = hoy[w] - db * (d1 - d2);
                 // H_z(i+1/2, j+1/2, p) -= dt/mu0 (dEy/dx - dEx/dy)
-                d1 = (eyx[r] - eyv[r]) * P.rdx;
-                d2 = (exv[r + 1] - exv[r]) * P.rdy;
+                d1 = (eyx[r] - eyv[r]) * rdx;
+                d2 = (exv[r + 1] - exv[r]) * rdy;
                 if (HPX && sx >= 0)
                     d1 = cpt(d1, pv[r][9], vz ? P.psiHw[0][1] + (p * NY1 + j) * L + sx : (T *)nullptr, PX, BX, 3, lx);
                 if (HPY && sy[r] >= 0)
                     d2 = cpt(d2, pv[r][1], vz ? P.psiHw[1][1] + (p * L + sy[r]) * px + i : (T *)nullptr, PY, WY, 3, ly);
-                hz[r] = hoz[w] - P.db * (d1 - d2);
+                hz[r] = hoz[w] - db * (d1 - d2);
                 sHn[w] = hx[r];
                 sHn[WN + w] = hy[r];
                 sHn[2 * WN + w] = hz[r];
                 const long q = qb + (long)r * px;
-                if (vx) P.B[3 * npts + q] = hx[r];
-                if (vy) P.B[4 * npts + q] = hy[r];
-                if (vz) P.B[5 * npts + q] = hz[r];
+                if (vx) Bo[3 * npts + q] = hx[r];
+                if (vy) Bo[4 * npts + q] = hy[r];
+                if (vz) Bo[5 * npts + q] = hz[r];
             }
             if (h_comp >= 0) {   // one halo H value per thread of the first warps
                 T v = 0;
                 if (h_live) {
                     const int w = h_w;
                     if (h_comp == 0) {
-                        T d1 = (ez0[w + BX] - ez0[w]) * P.rdy, d2 = (ey1[w] - ey0[w]) * P.rdz;
+                        T d1 = (ez0[w + BX] - ez0[w]) * rdy, d2 = (ey1[w] - ey0[w]) * rdz;
                         if (HPY && h_sy >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PY, WY, 3, h_ly);
                         if (HPZ && sz >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PZ, ZMAX, 3, lz);
-                        v = hox[w] - P.db * (d1 - d2);
+                        v = hox[w] - db * (d1 - d2);
                     } else if (h_comp == 1) {
-                        T d1 = (ex1[w] - ex0[w]) * P.rdz, d2 = (ez0[w + 1] - ez0[w]) * P.rdx;
+                        T d1 = (ex1[w] - ex0[w]) * rdz, d2 = (ez0[w + 1] - ez0[w]) * rdx;
                         if (HPZ && sz >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PZ, ZMAX, 3, lz);
                         if (HPX && h_sx >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PX, BX, 3, h_lx);
-                        v = hoy[w] - P.db * (d1 - d2);
+                        v = hoy[w] - db * (d1 - d2);
                     } else {
-                        T d1 = (ey0[w + 1] - ey0[w]) * P.rdx, d2 = (ex0[w + BX] - ex0[w]) * P.rdy;
+                        T d1 = (ey0[w + 1] - ey0[w]) * rdx, d2 = (ex0[w + BX] - ex0[w]) * rdy;
                         if (HPX && h_sx >= 0) d1 = cpt(d1, hv[0], (T *)nullptr, PX, BX, 3, h_lx);
                         if (HPY && h_sy >= 0) d2 = cpt(d2, hv[1], (T *)nullptr, PY, WY, 3, h_ly);
-                        v = hoz[w] - P.db * (d1 - d2);
+                        v = hoz[w] - db * (d1 - d2);
                     }
                 }
                 sHn[h_comp * WN + h_w] = v;
@@ -445,7 +450,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
                 T exn = 0, eyn = 0, ezn = 0;
                 int c = cl[crow];
                 if (c) {   // E_x(i+1/2, j, p) = Ca E_x + Cb (dHz/dy - dHy/dz)
-                    T d1 = (hz[r] - hz_up) * P.rdy, d2 = (hy[r] - hy_prev[r]) * P.rdz;
+                    T d1 = (hz[r] - hz_up) * rdy, d2 = (hy[r] - hy_prev[r]) * rdz;
                     if (HPY && sy[r] >= 0) d1 = cpt(d1, pv[r][2], P.psiE[1][0] + (p * L + sy[r]) * px + i, PY, WY, 0, ly);
                     if (HPZ && sz >= 0) d2 = cpt(d2, pv[r][6], P.psiE[2][0] + (sz * NY1 + j) * px + i, PZ, ZMAX, 0, lz);
                     const P2 k = sC[c];
@@ -453,7 +458,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
                 }
                 c = cl[TX * TY + crow];
                 if (c) {   // E_y(i, j+1/2, p) = Ca E_y + Cb (dHx/dz - dHz/dx)
-                    T d1 = (hx[r] - hx_prev[r]) * P.rdz, d2 = (hz[r] - shz[w - 1]) * P.rdx;
+                    T d1 = (hx[r] - hx_prev[r]) * rdz, d2 = (hz[r] - shz[w - 1]) * rdx;
                     if (HPZ && sz >= 0) d1 = cpt(d1, pv[r][7], P.psiE[2][1] + (sz * NY1 + j) * px + i, PZ, ZMAX, 0, lz);
                     if (HPX && sx >= 0) d2 = cpt(d2, pv[r][10], P.psiE[0][0] + (p * NY1 + j) * L + sx, PX, BX, 0, lx);
                     const P2 k = sC[c];
@@ -461,7 +466,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
                 }
                 c = cl[2 * TX * TY + crow];
                 if (c) {   // E_z(i, j, p+1/2) = Ca E_z + Cb (dHy/dx - dHx/dy)
-                    T d1 = (hy[r] - shy[w - 1]) * P.rdx, d2 = (hx[r] - hx_up) * P.rdy;
+                    T d1 = (hy[r] - shy[w - 1]) * rdx, d2 = (hx[r] - hx_up) * rdy;
                     if (HPX && sx >= 0) d1 = cpt(d1, pv[r][11], P.psiE[0][1] + (p * NY1 + j) * L + sx, PX, BX, 0, lx);
                     if (HPY && sy[r] >= 0) d2 = cpt(d2, pv[r][3], P.psiE[1][1] + (p * L + sy[r]) * px + i, PY, WY, 0, ly);
                     const P2 k = sC[c];
@@ -469,9 +474,9 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
                 }
                 if (rlive[r]) {
                     const long q = qb + (long)r * px;
-                    P.B[q] = exn;
-                    P.B[npts + q] = eyn;
-                    P.B[2 * npts + q] = ezn;
+                    Bo[q] = exn;
+                    Bo[npts + q] = eyn;
+                    Bo[2 * npts + q] = ezn;
                 }
                 hz_up = hz[r];
                 hx_up = hx[r];
