@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
 {
     __shared__ double red[kEpiThreads / 32];
     __shared__ double vi[kMaxPorts][2];
+    __shared__ double pval[kEpiThreads];
+    __shared__ int pdst[kEpiThreads];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const long long n = *P.ctr;   // this is step n: E^{n+1}, H^{n+1/2} are in place
@@ -299,13 +301,32 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (tid == 0) {
+    if (tid == 0)
         for (int p = 0; p < P.nports; ++p) { vi[p][0] = 0.0; vi[p][1] = 0.0; }
-        for (int sg = 0; sg < P.nseg; ++sg) {
+    // the block fetches the partials of up to kEpiThreads segments at once; thread 0 adds them
+    // in segment order
+    for (int c = 0; c < P.nseg; c += kEpiThreads) {
+        const int sg = c + tid;
+        int dst = -1;
+        double v = 0.0;
+        if (sg < P.nseg) {
             const EpiSeg S = P.segs[sg];
-            if (S.kind == 1) vi[S.port][0] += __ldcg(P.slots + sg);
-            else if (S.kind == 2) vi[S.port][1] += __ldcg(P.slots + sg);
+            if (S.kind != 0) {
+                dst = 2 * S.port + (S.kind == 2);
+                v = __ldcg(P.slots + sg);
+            }
         }
+        pdst[tid] = dst;
+        pval[tid] = v;
+        __syncthreads();
+        if (tid == 0) {
+            const int m = P.nseg - c < kEpiThreads ? P.nseg - c : kEpiThreads;
+            for (int q = 0; q < m; ++q)
+                if (pdst[q] >= 0) vi[pdst[q] >> 1][pdst[q] & 1] += pval[q];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
         epi_scale(P, vi);
         *P.ticket = 0;
     }
