@@ -224,7 +224,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     for (int q = tid; q < kMaxClasses; q += TBN) CT[q] = make_float2(P.ctab[2 * q], P.ctab[2 * q + 1]);
     __syncthreads();
 
-    auto issue = [&](int p) {   // thread 0: step-n plane p -> field stage p & 3, class slot p % 6
+    auto issue = [&](int p) {   // one thread: step-n plane p -> field stage p & 3, class slot p % 6
         unsigned char *st = sm + (p & 3) * 2 * PL;
         const uint32_t bar = bar0 + 8 * (p & 3);
         mbar_expect_tx(bar, TX_BYTES);
@@ -280,11 +280,6 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         } else {
             __syncthreads();
         }
-        // every thread has finished plane q-2's stage and plane q-4's classes: refill them
-        if (tid == 0 && q <= ke) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(q + 2);
-        }
         const int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;   // (q-3) mod 3, (q-2) mod 3
         const int p3 = q - 3;
         const float *f0 = reinterpret_cast<const float *>(sm + ((q - 1) & 3) * 2 * PL);   // step n, plane q-1
@@ -303,6 +298,13 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         if (T1.kind == 1 && q <= ke + 2) h_pair(f0, f1, f0 + 3 * WN, haw, T1.w, K, c1x, c1y, q > kb - 1);
         if (T1.kind == 3 && q >= kb + 2) h_pair(ea3, ea2, ha3, hb3, T1.w, K, c1x, c1y, q > kb + 2);
         __syncthreads();
+        // every thread finished plane q-2's stage and plane q-4's classes before this plane's
+        // first barrier, and phase 2 reads neither: the last warp, which has no phase-2 task,
+        // refills them with plane q+2
+        if (tid == TBN - 32 && q <= ke) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(q + 2);
+        }
         // phase 2: S2 on plane q-1, S4 on plane q-3 (into C)
         if (T2.kind == 2 && q >= kb && q <= ke + 2) {
             float2 vx, vy, vz;

@@ -209,13 +209,12 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int q = kb - 1, s = 0; q <= kb + 1 && q <= ke + 1; ++q, ++s) issue(q, s);
     }
-    // one thread polls the stage barrier; the others sleep in the block barrier
+    // first plane: one thread polls the stage barrier, the others sleep in the block barrier
+    // (every thread keeps the phase bits)
     auto wait_stage = [&](int s) -> bool {
         bool ok = true;
-        if (tid == 0) {
-            ok = mbar_wait(bar0 + 8 * s, (phase >> s) & 1u);
-            phase ^= 1u << s;
-        }
+        if (tid == 0) ok = mbar_wait(bar0 + 8 * s, (phase >> s) & 1u);
+        phase ^= 1u << s;
         return __syncthreads_and(ok);
     };
     if (!wait_stage(0)) {
@@ -326,12 +325,15 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 #pragma unroll
     for (int r = 0; r < CY; ++r) hx_prev[r] = hy_prev[r] = 0;
     int sp = 0, sn = 1;   // stages of planes p and p + 1
+    bool gave_up = false;
     for (int p = kb - 1; p <= ke; ++p) {
-        // plane p + 1 must have landed (its E is the upper neighbour of plane p's H)
-        if (!wait_stage(sn)) {
-            if (tid == 0) atomicOr(status, 2);
-            return;
-        }
+        // plane p + 1 must have landed (its E is the upper neighbour of plane p's H).  Every
+        // thread waits on the stage barrier itself: the end-of-plane barrier below already
+        // orders the last plane's reads of sHn before this plane's writes.  A thread whose
+        // wait gives up carries on (its results are discarded) and the block leaves together
+        // at that barrier.
+        gave_up |= !mbar_wait(bar0 + 8 * sn, (phase >> sn) & 1u);
+        phase ^= 1u << sn;
         const unsigned char *stp = sm + sp * Lay::STAGE;
         const unsigned char *stn = sm + sn * Lay::STAGE;
         const T *ex0 = reinterpret_cast<const T *>(stp), *ey0 = ex0 + WN, *ez0 = ey0 + WN;
@@ -487,7 +489,10 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
         // auxiliaries of the next plane, in flight during the barrier and the next wait
         fetch(p + 1);
         // every thread is done with stage sp: refill it with plane p + 3
-        __syncthreads();
+        if (__syncthreads_or(gave_up)) {
+            if (tid == 0) atomicOr(status, 2);
+            return;
+        }
         if (tid == 0 && p + 3 <= ke + 1) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(p + 3, sp);
