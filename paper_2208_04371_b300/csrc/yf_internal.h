@@ -187,7 +187,7 @@ void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, co
 // tile and TMA boxes of the two-step kernel
 constexpr int kTbTileX = 32, kTbTileY = 8;   // output tile
 constexpr int kTbWinX = 40, kTbWinY = 12;    // E and H windows: x from i0-4, y from j0-2
-constexpr int kTbClsX = 64, kTbClsY = 10;    // class tiles: x from i0-16, y from j0-1
+constexpr int kTbClsX = 80, kTbClsY = 10;    // class tiles: x from i0-16, y from j0-1
 struct TbArgs {
     int px;
     long plane, npts;

@@ -38,18 +38,24 @@ namespace {
 constexpr int TBX = kTbTileX, TBY = kTbTileY;         // output tile
 constexpr int NWARP = 12, TBN = 32 * NWARP;          // block
 constexpr int WXN = kTbWinX, WYN = kTbWinY, WN = WXN * WYN;   // windows: x from i0-4, y from j0-2
+// the rings the threads write (H^{n+1/2}, E^{n+1}, H^{n+3/2}) cover the same nodes with rows of
+// 44 floats: a 12-bank shift per row spreads the strips of eight rows over all 32 banks
+constexpr int WXR = 44, WR = WXR * WYN;
 constexpr int CXN = kTbClsX, CYN = kTbClsY, CN = CXN * CYN;   // class tile: x from i0-16, y from j0-1
+constexpr int CSLOT = (3 * CN + 127) / 128 * 128;    // one class slot (bytes)
 constexpr int FST = 4, CSL = 6;                      // field stages, class slots
-constexpr int PL = 3 * WN * 4;                       // one plane of three components (bytes)
+constexpr int PL = 3 * WN * 4;                       // one stage plane of three components (bytes)
+constexpr int PR = 3 * WR * 4;                       // one ring plane of three components (bytes)
 constexpr int C_OFF = FST * 2 * PL;                  // stage s: E at s * 2PL, H at s * 2PL + PL
-constexpr int HA_OFF = C_OFF + CSL * 3 * CN;         // H^{n+1/2} [3][3][WN]
-constexpr int EA_OFF = HA_OFF + 3 * PL;              // E^{n+1}   [3][3][WN]
-constexpr int HB_OFF = EA_OFF + 3 * PL;              // H^{n+3/2} [2][3][WN]
-constexpr int CT_OFF = HB_OFF + 2 * PL;              // (Ca, Cb) per class
+constexpr int HA_OFF = C_OFF + CSL * CSLOT;          // H^{n+1/2} [3][3][WR]
+constexpr int EA_OFF = HA_OFF + 3 * PR;              // E^{n+1}   [3][3][WR]
+constexpr int HB_OFF = EA_OFF + 3 * PR;              // H^{n+3/2} [2][3][WR]
+constexpr int CT_OFF = HB_OFF + 2 * PR;              // (Ca, Cb) per class
 constexpr int BAR_OFF = CT_OFF + 2 * kMaxClasses * 4;
 constexpr int TB_BYTES = BAR_OFF + 8 * FST;
 constexpr uint32_t TX_BYTES = 2 * PL + 3 * CN;
-static_assert(PL % 128 == 0 && C_OFF % 128 == 0 && (3 * CN) % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(PL % 128 == 0 && C_OFF % 128 == 0 && CSLOT % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(PR % 16 == 0 && HA_OFF % 16 == 0, "ring planes 16-byte aligned");
 static_assert(2 * (TB_BYTES + 1024) <= 228 * 1024, "two blocks per SM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -100,11 +106,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
 // S2 and S3 and on the right of S1 and S2; those extra nodes read neighbours nobody computed
 // and feed nothing.  The pair's values move as float2 (64-bit shared loads, one 32-bit load
 // for the neighbour shifted by one node in x) through Blackwell's paired FP32 arithmetic.
-// w, c: window and class-tile index of the pair's first node; g: its offset j px + i in a
+// w, v, c: window, ring and class-tile index of the pair's first node; g: its offset j px + i in a
 // field plane; own: the pair is in the block's tile; lay: a node of it lies on the box's
 // outer layer in x or y.
 struct Task {
-    int kind, w, c, g;
+    int kind, w, v, c, g;
     bool own, lay;
 };
 
@@ -121,7 +127,7 @@ __device__ __forceinline__ bool stage_pair(int e, int R, int extra, int *row, in
 
 __device__ __forceinline__ Task make_task(int phase, int tid, int i0, int j0, const TbArgs &P)
 {
-    Task k{0, 0, 0, 0, false, false};
+    Task k{0, 0, 0, 0, 0, false, false};
     int i = 0, j = 0, r, q;
     if (phase == 1) {
         if (tid < 224 && stage_pair(tid, 11, 2, &r, &q)) { k.kind = 1; i = i0 - 2 + 2 * q; j = j0 - 2 + r; }
@@ -132,6 +138,7 @@ __device__ __forceinline__ Task make_task(int phase, int tid, int i0, int j0, co
     }
     if (!k.kind) return k;
     k.w = (j - j0 + 2) * WXN + (i - i0 + 4);
+    k.v = (j - j0 + 2) * WXR + (i - i0 + 4);
     k.c = (j - j0 + 1) * CXN + (i - i0 + 16);
     k.g = j * P.px + i;
     k.own = i >= i0 && i + 1 < i0 + TBX && j >= j0 && j < j0 + TBY;
@@ -154,36 +161,41 @@ struct Coef {
 };
 
 // H update of a node pair (S1 from step-n data, S3 from E^{n+1}): e0/e1 = E on planes p, p+1,
-// h0 = H on plane p, all in window layout; result into hw
+// h0 = H on plane p, read at index w in rows of RS floats; result into the ring hw at index v
 // A thread keeps its stage and pair on every plane, so the E_x, E_y (or H_x, H_y) of the
 // pair that one plane reads as its upper (lower) z-neighbour are the next plane's centre
 // values: they are carried in registers (cx, cy) once the stage has run on a plane before.
+template <int RS>
 __device__ __forceinline__ void h_pair(const float *e0, const float *e1, const float *h0, float *hw, int w,
-                                       const Coef &K, float2 &cx, float2 &cy, bool carried)
+                                       int v, const Coef &K, float2 &cx, float2 &cy, bool carried)
 {
-    const float2 ex = carried ? cx : ld2(e0 + w), ey = carried ? cy : ld2(e0 + WN + w);
-    const float2 ez = ld2(e0 + 2 * WN + w);
-    const float2 exU = ld2(e0 + w + WXN), ezU = ld2(e0 + 2 * WN + w + WXN);
-    const float2 eyR = make_float2(ey.y, e0[WN + w + 2]), ezR = make_float2(ez.y, e0[2 * WN + w + 2]);
-    const float2 ex1 = ld2(e1 + w), ey1 = ld2(e1 + WN + w);
+    constexpr int RN = RS * WYN;   // one component of a plane
+    const float2 ex = carried ? cx : ld2(e0 + w), ey = carried ? cy : ld2(e0 + RN + w);
+    const float2 ez = ld2(e0 + 2 * RN + w);
+    const float2 exU = ld2(e0 + w + RS), ezU = ld2(e0 + 2 * RN + w + RS);
+    const float2 eyR = make_float2(ey.y, e0[RN + w + 2]), ezR = make_float2(ez.y, e0[2 * RN + w + 2]);
+    const float2 ex1 = ld2(e1 + w), ey1 = ld2(e1 + RN + w);
     cx = ex1;
     cy = ey1;
     // H_x -= dt/mu0 (dEz/dy - dEy/dz), H_y -= dt/mu0 (dEx/dz - dEz/dx), H_z -= dt/mu0 (dEy/dx - dEx/dy)
-    st2(hw + w, __ffma2_rn(curl(dif(ezU, ez), K.ry, dif(ey1, ey), K.nrz), K.ndb, ld2(h0 + w)));
-    st2(hw + WN + w, __ffma2_rn(curl(dif(ex1, ex), K.rz, dif(ezR, ez), K.nrx), K.ndb, ld2(h0 + WN + w)));
-    st2(hw + 2 * WN + w, __ffma2_rn(curl(dif(eyR, ey), K.rx, dif(exU, ex), K.nry), K.ndb, ld2(h0 + 2 * WN + w)));
+    st2(hw + v, __ffma2_rn(curl(dif(ezU, ez), K.ry, dif(ey1, ey), K.nrz), K.ndb, ld2(h0 + w)));
+    st2(hw + WR + v, __ffma2_rn(curl(dif(ex1, ex), K.rz, dif(ezR, ez), K.nrx), K.ndb, ld2(h0 + RN + w)));
+    st2(hw + 2 * WR + v, __ffma2_rn(curl(dif(eyR, ey), K.rx, dif(exU, ex), K.nry), K.ndb, ld2(h0 + 2 * RN + w)));
 }
 
-// E update of a node pair: eo = E before, ha/hp = H on planes k, k-1, cl = class tile of
-// plane k.  Class 0 (PEC) has Ca = Cb = 0, so its edges stay zero.
-__device__ __forceinline__ void e_pair(const float *eo, const float *ha, const float *hp, const unsigned char *cl,
-                                       const float2 *CT, int w, int c, const Coef &K, float2 *vx, float2 *vy,
-                                       float2 *vz, float2 &cx, float2 &cy, bool carried)
+// E update of a node pair: eo = E before (index we in rows of ES floats), ha/hp = H on planes
+// k, k-1 (ring index v), cl = class tile of plane k.  Class 0 (PEC) has Ca = Cb = 0, so its
+// edges stay zero.
+template <int ES>
+__device__ __forceinline__ void e_pair(const float *eo, int we, const float *ha, const float *hp, int v,
+                                       const unsigned char *cl, const float2 *CT, int c, const Coef &K, float2 *vx,
+                                       float2 *vy, float2 *vz, float2 &cx, float2 &cy, bool carried)
 {
-    const float2 hx = ld2(ha + w), hy = ld2(ha + WN + w), hz = ld2(ha + 2 * WN + w);
-    const float2 hxD = ld2(ha + w - WXN), hzD = ld2(ha + 2 * WN + w - WXN);
-    const float2 hyL = make_float2(ha[WN + w - 1], hy.x), hzL = make_float2(ha[2 * WN + w - 1], hz.x);
-    const float2 hpx = carried ? cx : ld2(hp + w), hpy = carried ? cy : ld2(hp + WN + w);
+    constexpr int EN = ES * WYN;
+    const float2 hx = ld2(ha + v), hy = ld2(ha + WR + v), hz = ld2(ha + 2 * WR + v);
+    const float2 hxD = ld2(ha + v - WXR), hzD = ld2(ha + 2 * WR + v - WXR);
+    const float2 hyL = make_float2(ha[WR + v - 1], hy.x), hzL = make_float2(ha[2 * WR + v - 1], hz.x);
+    const float2 hpx = carried ? cx : ld2(hp + v), hpy = carried ? cy : ld2(hp + WR + v);
     cx = hx;
     cy = hy;
     const unsigned cxx = *reinterpret_cast<const unsigned short *>(cl + c);
@@ -195,11 +207,11 @@ __device__ __forceinline__ void e_pair(const float *eo, const float *ha, const f
     // E_x = Ca E_x + Cb (dHz/dy - dHy/dz), E_y = Ca E_y + Cb (dHx/dz - dHz/dx),
     // E_z = Ca E_z + Cb (dHy/dx - dHx/dy)
     *vx = __ffma2_rn(make_float2(ax0.y, ax1.y), curl(dif(hz, hzD), K.ry, dif(hy, hpy), K.nrz),
-                     __fmul2_rn(make_float2(ax0.x, ax1.x), ld2(eo + w)));
+                     __fmul2_rn(make_float2(ax0.x, ax1.x), ld2(eo + we)));
     *vy = __ffma2_rn(make_float2(ay0.y, ay1.y), curl(dif(hx, hpx), K.rz, dif(hz, hzL), K.nrx),
-                     __fmul2_rn(make_float2(ay0.x, ay1.x), ld2(eo + WN + w)));
+                     __fmul2_rn(make_float2(ay0.x, ay1.x), ld2(eo + EN + we)));
     *vz = __ffma2_rn(make_float2(az0.y, az1.y), curl(dif(hy, hyL), K.rx, dif(hx, hxD), K.nry),
-                     __fmul2_rn(make_float2(az0.x, az1.x), ld2(eo + 2 * WN + w)));
+                     __fmul2_rn(make_float2(az0.x, az1.x), ld2(eo + 2 * EN + we)));
 }
 
 __global__ void __launch_bounds__(TBN, 2)
@@ -230,7 +242,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         mbar_expect_tx(bar, TX_BYTES);
         tma_load_4d(smem_u32(st), tmW, i0 - 4, j0 - 2, p, 0, bar);
         tma_load_4d(smem_u32(st + PL), tmW, i0 - 4, j0 - 2, p, 3, bar);
-        tma_load_4d(smem_u32(sm + C_OFF + (p % CSL) * 3 * CN), tmC, i0 - 16, j0 - 1, p, 0, bar);
+        tma_load_4d(smem_u32(sm + C_OFF + (p % CSL) * CSLOT), tmC, i0 - 16, j0 - 1, p, 0, bar);
     };
     uint32_t ph = 0;   // thread 0: parity of each stage's next completion
     auto wait_plane = [&](int p) -> bool {
@@ -284,19 +296,19 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         const int p3 = q - 3;
         const float *f0 = reinterpret_cast<const float *>(sm + ((q - 1) & 3) * 2 * PL);   // step n, plane q-1
         const float *f1 = reinterpret_cast<const float *>(sm + (q & 3) * 2 * PL);         // step n, plane q
-        float *haw = HA + a * 3 * WN;                 // H^{n+1/2} plane q-1
-        const float *hap = HA + a2 * 3 * WN;          // plane q-2
-        const float *ha3 = HA + a1 * 3 * WN;          // plane q-3
-        float *eaw = EA + a * 3 * WN;                 // E^{n+1} plane q-1
-        const float *ea3 = EA + a1 * 3 * WN, *ea2 = EA + a2 * 3 * WN;
-        float *hb3 = HB + (p3 & 1) * 3 * WN;          // H^{n+3/2} plane q-3
-        const float *hb4 = HB + ((p3 + 1) & 1) * 3 * WN;
-        const unsigned char *cl1 = sm + C_OFF + b * 3 * CN;
-        const unsigned char *cl3 = sm + C_OFF + (b >= 2 ? b - 2 : b + 4) * 3 * CN;
+        float *haw = HA + a * 3 * WR;                 // H^{n+1/2} plane q-1
+        const float *hap = HA + a2 * 3 * WR;          // plane q-2
+        const float *ha3 = HA + a1 * 3 * WR;          // plane q-3
+        float *eaw = EA + a * 3 * WR;                 // E^{n+1} plane q-1
+        const float *ea3 = EA + a1 * 3 * WR, *ea2 = EA + a2 * 3 * WR;
+        float *hb3 = HB + (p3 & 1) * 3 * WR;          // H^{n+3/2} plane q-3
+        const float *hb4 = HB + ((p3 + 1) & 1) * 3 * WR;
+        const unsigned char *cl1 = sm + C_OFF + b * CSLOT;
+        const unsigned char *cl3 = sm + C_OFF + (b >= 2 ? b - 2 : b + 4) * CSLOT;
 
         // phase 1: S1 on plane q-1, S3 on plane q-3
-        if (T1.kind == 1 && q <= ke + 2) h_pair(f0, f1, f0 + 3 * WN, haw, T1.w, K, c1x, c1y, q > kb - 1);
-        if (T1.kind == 3 && q >= kb + 2) h_pair(ea3, ea2, ha3, hb3, T1.w, K, c1x, c1y, q > kb + 2);
+        if (T1.kind == 1 && q <= ke + 2) h_pair<WXN>(f0, f1, f0 + 3 * WN, haw, T1.w, T1.v, K, c1x, c1y, q > kb - 1);
+        if (T1.kind == 3 && q >= kb + 2) h_pair<WXR>(ea3, ea2, ha3, hb3, T1.v, T1.v, K, c1x, c1y, q > kb + 2);
         __syncthreads();
         // every thread finished plane q-2's stage and plane q-4's classes before this plane's
         // first barrier, and phase 2 reads neither: the last warp, which has no phase-2 task,
@@ -308,10 +320,10 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         // phase 2: S2 on plane q-1, S4 on plane q-3 (into C)
         if (T2.kind == 2 && q >= kb && q <= ke + 2) {
             float2 vx, vy, vz;
-            e_pair(f0, haw, hap, cl1, CT, T2.w, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb);
-            st2(eaw + T2.w, vx);
-            st2(eaw + WN + T2.w, vy);
-            st2(eaw + 2 * WN + T2.w, vz);
+            e_pair<WXN>(f0, T2.w, haw, hap, T2.v, cl1, CT, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb);
+            st2(eaw + T2.v, vx);
+            st2(eaw + WR + T2.v, vy);
+            st2(eaw + 2 * WR + T2.v, vz);
             // the box's outer node layer at n + 1 (and its H^{n+1/2}) for the frame's second
             // step; a pair with one layer node writes both (the other value is also correct)
             const int k = q - 1;
@@ -320,21 +332,21 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
                 st2(B, vx);
                 st2(B + npts, vy);
                 st2(B + 2 * npts, vz);
-                st2(B + 3 * npts, ld2(haw + T2.w));
-                st2(B + 4 * npts, ld2(haw + WN + T2.w));
-                st2(B + 5 * npts, ld2(haw + 2 * WN + T2.w));
+                st2(B + 3 * npts, ld2(haw + T2.v));
+                st2(B + 4 * npts, ld2(haw + WR + T2.v));
+                st2(B + 5 * npts, ld2(haw + 2 * WR + T2.v));
             }
         }
         if (T2.kind == 4 && q >= kb + 3) {
             float2 vx, vy, vz;
-            e_pair(ea3, hb3, hb4, cl3, CT, T2.w, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb + 3);
+            e_pair<WXR>(ea3, T2.v, hb3, hb4, T2.v, cl3, CT, T2.c, K, &vx, &vy, &vz, c2x, c2y, q > kb + 3);
             float *C = P.C + (p3 * plane + T2.g);
             st2(C, vx);
             st2(C + npts, vy);
             st2(C + 2 * npts, vz);
-            st2(C + 3 * npts, ld2(hb3 + T2.w));
-            st2(C + 4 * npts, ld2(hb3 + WN + T2.w));
-            st2(C + 5 * npts, ld2(hb3 + 2 * WN + T2.w));
+            st2(C + 3 * npts, ld2(hb3 + T2.v));
+            st2(C + 4 * npts, ld2(hb3 + WR + T2.v));
+            st2(C + 5 * npts, ld2(hb3 + 2 * WR + T2.v));
         }
         a = a == 2 ? 0 : a + 1;
         b = b == CSL - 1 ? 0 : b + 1;
