@@ -101,7 +101,7 @@ static yf_status derive_materials(yf_grid *g, const uint8_t *ids_dev, int nmat, 
                                   const double *sigma, const uint8_t *is_pec)
 {
     yf_status st = derive_edge_classes(g->nx, g->ny, g->nz, g->px, g->plane, ids_dev, nmat, eps_r,
-                                       sigma, is_pec, g->cls, &g->mat, g->stream);
+                                       sigma, is_pec, g->cls, &g->mat, &g->mat_scratch, g->stream);
     if (st != YF_OK) return st;
     st = build_coeff_tables(g);
     if (st != YF_OK) return st;
@@ -604,6 +604,8 @@ yf_status yf_grid_destroy(yf_grid *g)
     cudaFree(g->ctab); cudaFree(g->eps_tab); cudaFree(g->ctr); cudaFree(g->status);
     cudaFree(g->energy_partials); cudaFree(g->ports_dev); cudaFree(g->inc_dev);
     cudaFree(g->acc64); cudaFree(g->acc32); cudaFree(g->kahan); cudaFree(g->src_table_dev);
+    cudaFree(g->ids_stage);
+    mat_scratch_free(&g->mat_scratch);
     if (g->own_stream) cudaStreamDestroy(g->stream);
     delete g;
     return YF_OK;
@@ -632,15 +634,22 @@ yf_status yf_set_materials(yf_grid *g, const uint8_t *ids, yf_mem where, int nma
     }
     const size_t ncell = (size_t)g->nx * g->ny * g->nz;
     const uint8_t *ids_dev = ids;
-    uint8_t *tmp = nullptr;
+    // host ids go through a device staging buffer on the grid's stream; a grid that re-solves
+    // after yf_reset keeps that buffer, one set up once (a batch instance) frees it
+    const bool keep = g->started;
     if (where == YF_HOST) {
-        YF_CUDA_TRY(cudaMalloc(&tmp, ncell));
-        cudaError_t e = cudaMemcpy(tmp, ids, ncell, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { cudaFree(tmp); return cuda_fail(e, "copying ids"); }
-        ids_dev = tmp;
+        if (!g->ids_stage) YF_CUDA_TRY(cudaMalloc(&g->ids_stage, ncell));
+        YF_CUDA_TRY(cudaMemcpyAsync(g->ids_stage, ids, ncell, cudaMemcpyHostToDevice, g->stream));
+        ids_dev = g->ids_stage;
     }
     yf_status st = derive_materials(g, ids_dev, nmat, eps_r, sigma, is_pec);
-    if (tmp) cudaFree(tmp);
+    if (where == YF_HOST) {
+        cudaStreamSynchronize(g->stream);   // the copy has read the caller's ids, also on errors
+        if (!keep) {
+            cudaFree(g->ids_stage);
+            g->ids_stage = nullptr;
+        }
+    }
     return st;
 }
 

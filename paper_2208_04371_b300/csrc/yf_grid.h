@@ -89,6 +89,8 @@ struct yf_grid {
     int chunk = 32;               // steps per captured graph (even)
     cudaGraphExec_t graph[6] = {};   // one per starting state cur * 2 + hpar
     yf::TbPlan *tb = nullptr;        // variant 4
+    yf::MatScratch mat_scratch;      // device scratch of the class derivation
+    uint8_t *ids_stage = nullptr;    // host material ids staged on the device (re-solving grids)
 };
 
 namespace yf {

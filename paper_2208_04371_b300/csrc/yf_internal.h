@@ -233,10 +233,17 @@ struct MaterialResult {
     int nclass;                       // including class 0
     std::vector<double> eps_r, sigma; // per class (class 0 unused)
 };
+// device scratch of the class derivation, allocated on first use and kept by its owner
+struct MatScratch {
+    uint32_t *table = nullptr;
+    uint8_t *slot_class = nullptr, *pec = nullptr, *uni = nullptr;
+    int *overflow = nullptr;
+};
+void mat_scratch_free(MatScratch *m);
 yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const uint8_t *ids_dev,
                               int nmat, const double *eps_r, const double *sigma,
                               const uint8_t *is_pec, uint8_t *cls_dev[3], MaterialResult *res,
-                              cudaStream_t s);
+                              MatScratch *scratch, cudaStream_t s);
 yf_status apply_pec_sheet(int nx, int ny, int nz, int px, long plane, uint8_t *cls_dev[3],
                           const int sheet[6], cudaStream_t s);
 

@@ -223,29 +223,30 @@ __global__ void k_sheet(uint8_t *ca, uint8_t *cb, int px, long plane, int ax, in
 yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const uint8_t *ids_dev,
                               int nmat, const double *eps_r, const double *sigma,
                               const uint8_t *is_pec, uint8_t *cls_dev[3], MaterialResult *res,
-                              cudaStream_t s)
+                              MatScratch *scratch, cudaStream_t s)
 {
     uint8_t pec_h[256];
     memset(pec_h, 0, sizeof(pec_h));
     for (int m = 0; m < nmat; ++m) pec_h[m] = is_pec ? (is_pec[m] ? 1 : 0) : 0;
 
-    uint32_t *table = nullptr;
-    uint8_t *slot_class = nullptr, *pec_d = nullptr, *uni_d = nullptr;
     std::vector<uint8_t> uni_h(256, 0);
-    int *overflow = nullptr;
     yf_status st = YF_OK;
     std::vector<uint32_t> keys(kHashSize);
     std::vector<uint8_t> slot_h(kHashSize, 0);
     KeyArgs A;
     int ovf = 0;
     const dim3 blk(256), grd(1, std::min(ny + 1, 128), std::min(nz + 1, 8));
-    if (cudaMalloc(&table, kHashSize * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&slot_class, kHashSize) != cudaSuccess || cudaMalloc(&pec_d, 256) != cudaSuccess ||
-        cudaMalloc(&uni_d, 256) != cudaSuccess ||
-        cudaMalloc(&overflow, sizeof(int)) != cudaSuccess) {
-        st = fail(YF_E_OOM, "derive_edge_classes: device allocation failed");
-        goto done;
+    if (!scratch->table &&
+        (cudaMalloc(&scratch->table, kHashSize * sizeof(uint32_t)) != cudaSuccess ||
+         cudaMalloc(&scratch->slot_class, kHashSize) != cudaSuccess || cudaMalloc(&scratch->pec, 256) != cudaSuccess ||
+         cudaMalloc(&scratch->uni, 256) != cudaSuccess ||
+         cudaMalloc(&scratch->overflow, sizeof(int)) != cudaSuccess)) {
+        mat_scratch_free(scratch);
+        return fail(YF_E_OOM, "derive_edge_classes: device allocation failed");
     }
+    uint32_t *const table = scratch->table;
+    uint8_t *const slot_class = scratch->slot_class, *const pec_d = scratch->pec, *const uni_d = scratch->uni;
+    int *const overflow = scratch->overflow;
     if (cudaMemsetAsync(table, 0xFF, kHashSize * sizeof(uint32_t), s) != cudaSuccess ||
         cudaMemsetAsync(overflow, 0, sizeof(int), s) != cudaSuccess ||
         cudaMemcpyAsync(pec_d, pec_h, 256, cudaMemcpyHostToDevice, s) != cudaSuccess) {
@@ -319,12 +320,17 @@ yf_status derive_edge_classes(int nx, int ny, int nz, int px, long plane, const 
         goto done;
     }
 done:
-    if (table) cudaFree(table);
-    if (slot_class) cudaFree(slot_class);
-    if (pec_d) cudaFree(pec_d);
-    if (uni_d) cudaFree(uni_d);
-    if (overflow) cudaFree(overflow);
     return st;
+}
+
+void mat_scratch_free(MatScratch *m)
+{
+    cudaFree(m->table);
+    cudaFree(m->slot_class);
+    cudaFree(m->pec);
+    cudaFree(m->uni);
+    cudaFree(m->overflow);
+    *m = MatScratch{};
 }
 
 yf_status apply_pec_sheet(int nx, int ny, int nz, int px, long plane, uint8_t *cls_dev[3],

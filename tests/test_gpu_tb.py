@@ -225,3 +225,29 @@ def test_pec_cavity_variant4_matches_variant2(gpu):
             g.sync()
             out[v] = g.fields()
     assert rel_l2(out[4], out[2]) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [2, 4])
+def test_reset_and_new_materials_resolve_bitwise(gpu, variant):
+    """yf_reset, yf_set_materials from host memory (pageable, then pinned) and the PEC sheets
+    again: a solve with other materials between two solves of the same problem leaves the
+    third solve equal to the first bit for bit (fields and spectra), the path a re-solving
+    caller takes.  The second solve differs from both."""
+    import torch
+    p = _tb_problem()
+    ids_b = p.ids.copy()
+    ids_b[10:30, 20:40, 50:90] = 3
+    runs = []
+    with gpu.Grid(p, prec=gpu.FP32, variant=variant) as g:
+        for q, ids in enumerate((p.ids, ids_b, torch.from_numpy(p.ids).pin_memory())):
+            if q > 0:
+                gpu.reset(g.h)
+                gpu.set_materials(g.h, ids, p.eps_r, p.sigma, p.mu_r, p.is_pec)
+                for sh in p.sheets:
+                    gpu.add_pec_sheet(g.h, *sh)
+            g.step(61)
+            g.sync()
+            runs.append((g.fields(), *g.port_dfts()))
+    assert np.array_equal(runs[2][0], runs[0][0])
+    assert np.array_equal(runs[2][1], runs[0][1]) and np.array_equal(runs[2][2], runs[0][2])
+    assert not np.array_equal(runs[1][0], runs[0][0])
