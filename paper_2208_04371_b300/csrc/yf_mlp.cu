@@ -215,6 +215,15 @@ __device__ __forceinline__ float gelu(float x)
     const float th = tanh_hw(kGeluC * (x + kGeluA * x * x * x));
     return 0.5f * x * (1.f + th);
 }
+// the same on a pair of values through the paired FP32 instructions: (kA x) x, then
+// fma(., x, x), times kC; 0.5 x (1 + tanh)
+__device__ __forceinline__ float2 gelu2(float2 x)
+{
+    const float2 u = __fmul2_rn(make_float2(kGeluC, kGeluC),
+                                __ffma2_rn(__fmul2_rn(__fmul2_rn(make_float2(kGeluA, kGeluA), x), x), x, x));
+    const float2 s = __fadd2_rn(make_float2(1.f, 1.f), make_float2(tanh_hw(u.x), tanh_hw(u.y)));
+    return __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), x), s);
+}
 __device__ __forceinline__ float gelu_grad(float x)
 {
     const float th = tanh_hw(kGeluC * (x + kGeluA * x * x * x));
@@ -318,10 +327,14 @@ __device__ __forceinline__ void epi_hidden_staged(const GemmArgs &g, const uint3
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const float4 b4 = reinterpret_cast<const float4 *>(bias + q)[i];
-        v[4 * i] = gelu(__uint_as_float(r[4 * i]) + b4.x);
-        v[4 * i + 1] = gelu(__uint_as_float(r[4 * i + 1]) + b4.y);
-        v[4 * i + 2] = gelu(__uint_as_float(r[4 * i + 2]) + b4.z);
-        v[4 * i + 3] = gelu(__uint_as_float(r[4 * i + 3]) + b4.w);
+        const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1])),
+                                          make_float2(b4.x, b4.y)));
+        const float2 b = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])),
+                                          make_float2(b4.z, b4.w)));
+        v[4 * i] = a.x;
+        v[4 * i + 1] = a.y;
+        v[4 * i + 2] = b.x;
+        v[4 * i + 3] = b.y;
     }
     uint4 *srow = reinterpret_cast<uint4 *>(stg + lane * kStageRow);
 #pragma unroll
