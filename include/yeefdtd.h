@@ -117,7 +117,13 @@ yf_status yf_grid_dt(yf_grid *g, double *dt);
  * and sigma of the four cells sharing it and becomes PEC if any of them is PEC; the
  * update is the time-centred conductor form Ca = (1-L)/(1+L), Cb = (dt/eps)/(1+L),
  * L = sigma dt / (2 eps).  More than 255 distinct non-PEC edge materials returns
- * YF_E_UNSUPPORTED, as does any mu_r != 1.  mu_r may be NULL. */
+ * YF_E_UNSUPPORTED, as does any mu_r != 1.  mu_r may be NULL.
+ * ids with where == YF_HOST (pageable or pinned) are copied on the grid's stream into a
+ * device staging buffer of nz*ny*nx bytes; the call returns after the copy and the derivation
+ * have finished, so the caller may reuse its array at once.  A grid that has already stepped
+ * (a re-solve after yf_reset) keeps that buffer until yf_grid_destroy; otherwise it is freed
+ * before the call returns.  A small device scratch of the derivation (about 82 KB) is kept
+ * per grid. */
 yf_status yf_set_materials(yf_grid *g, const uint8_t *ids, yf_mem where, int nmat,
                            const double *eps_r, const double *sigma, const double *mu_r,
                            const uint8_t *is_pec);
