@@ -18,6 +18,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -70,10 +71,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, directory: str = ""):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples (the JSON line carries their summary); --clocks-dir keeps them
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"yf_bench_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
@@ -302,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
         g.step(chunk)
     g.sync()
 
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(local_rank, args.clocks_dir)
     sampler.start()
     barrier()
     torch.cuda.synchronize()
@@ -433,6 +435,8 @@ def main():
     ap.add_argument("--nz", type=int, default=256,
                     help="planes of the lossy line (profiling captures only; the bench line is nz=256)")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--clocks-dir", default="",
+                    help="directory for the raw nvidia-smi clock samples (default: the system temp directory)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
