@@ -251,3 +251,27 @@ def test_reset_and_new_materials_resolve_bitwise(gpu, variant):
     assert np.array_equal(runs[2][0], runs[0][0])
     assert np.array_equal(runs[2][1], runs[0][1]) and np.array_equal(runs[2][2], runs[0][2])
     assert not np.array_equal(runs[1][0], runs[0][0])
+
+
+def test_single_tile_box_matches_variant2(gpu):
+    """A 67 x 19 x 20 closed PEC cavity from seeded random fields: its box is one 32 x 8 tile
+    (x 32..63, y 8..15, z 3..17), so a single block writes the outer node layer on all four
+    sides and both z faces.  301 steps (150 pairs and one single step), two-step path against
+    one-step within the FP32 budget."""
+    nx, ny, nz = 67, 19, 20
+    p = W.Problem(nx=nx, ny=ny, nz=nz, dx=1e-3, dy=0.9e-3, dz=1.2e-3, courant=0.95,
+                  ids=np.zeros((nz, ny, nx), np.uint8), eps_r=np.array([1.0]),
+                  sigma=np.array([0.0]), mu_r=np.array([1.0]), is_pec=np.array([0], np.uint8),
+                  bc=(0,) * 6, pml_cells=0)
+    f0 = W.uniform_array(0x1713, 6 * (nz + 1) * (ny + 1) * (nx + 1), -1.0, 1.0).reshape(
+        6, nz + 1, ny + 1, nx + 1)
+    out = {}
+    for v in (2, 4):
+        with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
+            if v == 4:
+                assert gpu.tb_box(g.h) == (32, 63, 8, 15, 3, 17)
+            g.set_fields(f0)
+            g.step(301)
+            g.sync()
+            out[v] = g.fields()
+    assert rel_l2(out[4], out[2]) <= 1e-5
