@@ -275,3 +275,22 @@ def test_single_tile_box_matches_variant2(gpu):
             g.sync()
             out[v] = g.fields()
     assert rel_l2(out[4], out[2]) <= 1e-5
+
+
+def test_variant4_refuses_grids_beyond_its_32_bit_offsets(gpu):
+    """The two-step kernel addresses a buffer's six components with 32-bit offsets, so a grid
+    of more than (2^31 - 1) / 6 padded points is refused with YF_E_INVALID at its first step,
+    before any launch, and the context stays usable.  1023 x 511 x 682 cells are 1024 x 512 x
+    683 padded points: 6 x 358.1 M = 2.1485e9, just above 2^31 - 1 (the fields take 26 GB)."""
+    h = gpu.grid_create(1023, 511, 682, 1e-6, 1e-6, 1e-6, prec=gpu.FP32)
+    try:
+        gpu.set_variant(h, 4, 8, 32)
+        with pytest.raises(gpu.YFError) as e:
+            gpu.step(h, 2)
+        assert e.value.code == gpu.E_INVALID
+    finally:
+        gpu.grid_destroy(h)
+    with gpu.Grid(_tb_problem(), prec=gpu.FP32, variant=4) as g:
+        g.step(3)
+        g.sync()
+        assert np.isfinite(g.fields()).all()
