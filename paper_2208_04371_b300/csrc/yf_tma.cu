@@ -10,8 +10,10 @@
 // of plane q into stage q mod 3, completing on that stage's mbarrier.  Planes are issued
 // three ahead of the one being computed, so HBM latency overlaps the arithmetic of the two
 // planes before.  The x origin i0 - XO is a multiple of 16 bytes (XO = 16 / sizeof(T)); nodes
-// outside the grid arrive as zeros (TMA out-of-bounds fill).  Every mbarrier wait is bounded:
-// on expiry the block sets bit 1 of the status word and returns.
+// outside the grid arrive as zeros (TMA out-of-bounds fill).  Every thread waits on the
+// stage's mbarrier itself, and every wait is bounded: a thread whose wait expires finishes the
+// plane, then the block sets bit 1 of the status word and returns together at the plane's end
+// barrier.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
