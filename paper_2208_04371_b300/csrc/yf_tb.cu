@@ -16,9 +16,11 @@
 // z is marched with the stages skewed so that each plane iteration q has two phases separated
 // by one block barrier: {S1 on plane q-1, S3 on plane q-3}, then {S2 on plane q-1, S4 on
 // plane q-3}; every input of a phase comes from an earlier phase.  Step-n planes arrive by TMA
-// two planes ahead: E and H windows of 40 x 12 nodes (x from i0-4, y from j0-2) in four
-// stages, the class tiles (64 x 10) in six slots (S4 reads the classes of plane q-3).
-// H^{n+1/2} and E^{n+1} are kept for three planes, H^{n+3/2} for two.
+// two planes ahead (the last warp, idle in the second phase, issues each refill there): E and
+// H windows of 40 x 12 nodes (x from i0-4, y from j0-2) in four stages, the class tiles
+// (80 x 10 bytes) in six slots (S4 reads the classes of plane q-3).  H^{n+1/2} and E^{n+1} are
+// kept for three planes, H^{n+3/2} for two, in rings over the same nodes with rows of 44
+// floats, so that the strip tasks of eight rows fall in distinct banks.
 //
 // The single-step frame advances the rest of the grid n -> n+1 (A -> B) and n+1 -> n+2
 // (B -> C).  Its second step reads the box's outermost node layer at n + 1 from B (a window
