@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py: the reference arm's JSON line (the oracle on a bounded
-sample) and the rule that the stored stencil traffic is dropped once the stencil changes."""
+sample), the rule that the stored stencil traffic is dropped once the stencil changes, and
+where the raw clock samples are written."""
 import json
 import os
 import shutil
@@ -43,3 +44,19 @@ def test_stored_traffic_is_dropped_when_the_stencil_changes(tmp_path, monkeypatc
     (fake / "paper_2208_04371_b300" / "csrc" / "yf_tma.cu").write_bytes(src + b"\n")
     monkeypatch.setattr(bench, "ROOT", str(fake))
     assert bench.stencil_traffic("k_yee_tma_batch") is None
+
+
+def test_clock_samples_go_to_the_temp_directory_unless_given_one(tmp_path):
+    sys.path.insert(0, ROOT)
+    import tempfile
+
+    import bench
+    s = bench.ClockSampler(3)
+    assert os.path.dirname(s.path) == tempfile.gettempdir()
+    assert os.path.basename(s.path) == "yf_bench_clocks_rank3.csv"
+    s = bench.ClockSampler(0, str(tmp_path))
+    assert s.path == os.path.join(str(tmp_path), "yf_bench_clocks_rank0.csv")
+    # without nvidia-smi (or a GPU) the sampler reports that nothing was sampled
+    if shutil.which("nvidia-smi") is None:
+        s.start()
+        assert s.stop()["reasons"] == ["unsampled"]
