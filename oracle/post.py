@@ -18,6 +18,9 @@ Readings of the paper taken here (the printed text is garbled or silent):
     the new 50 ohm reference, not complex conjugation, so B* = B and A* = A;
     A = G*^{-1} G (I - B).
   * theta = -unwrap(arg S*_21), so tau > 0 under the e^{-j omega t} DFT sign.
+  * Uniform-line mode: port 1's reference is the forward wave's V/I with I taken
+    along +x (against port 1's own direction); a synthetic forward wave with
+    unequal references pins it (tests/test_oracle_post.py).
   * Eq. 7 (lossless line between 50 ohm ports): the printed S21 numerator
     (1 - kappa^2) kappa breaks |S11|^2 + |S21|^2 = 1; the textbook numerator
     (1 - Gamma^2) kappa is used, with kappa = e^{-j beta l} under this DFT sign.

@@ -30,9 +30,14 @@
  *
  * Parity pins (tests/test_oracle_*.py): exact discrete cavity eigenmodes (the
  * Yee dispersion relation), the discrete energy invariant of a lossless PEC
- * cavity, the Courant limit, brute-force PML reflection against a long domain.
- * The PML profile constants, the interface-averaging rule and the I-loop
- * margin have no physics pin: parity unpinned beyond GPU-vs-oracle.
+ * cavity, the Courant limit, brute-force PML reflection against a long domain;
+ * the conductor coefficients by a lossy-filled cavity mode against the exact
+ * recurrence of the time-centred conduction term (a dielectric loss and a
+ * metal whose E factor is negative); the port voltage by a field linear across
+ * the strip, which the trapezoid sum integrates exactly; the loop current by
+ * the discrete Ampere law (loop sum of H = enclosed eps dE_x/dt flux).
+ * The PML profile constants, the interface-averaging rule and the choice of
+ * the I-loop margin have no physics pin: parity unpinned beyond GPU-vs-oracle.
  */
 #include <math.h>
 #include <stdint.h>

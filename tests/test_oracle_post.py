@@ -154,3 +154,28 @@ def test_rlcg_of_a_lossless_line_has_no_loss_terms():
     w = 2 * np.pi * freqs
     assert np.all(np.abs(out["R"]) <= 1e-8 * w * L) and np.all(np.abs(out["G"]) <= 1e-8 * w * C)
     assert np.allclose(out["L"], L, rtol=1e-10) and np.allclose(out["C"], C, rtol=1e-10)
+
+
+@pytest.mark.parametrize("z0a,z0b", [(30.0, 80.0), (55.0 - 10j, 20.0 + 4j)])
+def test_sstar_uniform_recovers_kappa_and_both_references(z0a, z0b):
+    """Uniform-line mode (one run, S*_11 = 0): a forward wave that leaves port 0 with
+    V0 = a, I0 = a / Z0a (current along port 0's +x) and reaches port 1 as
+    V1 = kappa a sqrt(Z0b / Z0a), I1 = V1 / Z0b flowing along +x, i.e. recorded as -I1 in
+    port 1's own -x direction.  Power-mode transmission b_1 / a_0 = (V1/sqrt Z0b)/(V0/sqrt
+    Z0a) = kappa, and each port's reference is its own wave impedance.  The unequal
+    references make a wrong sign of port 1's current, which only rotates sqrt(Z_r0/Z_r1) by
+    90 degrees, visible."""
+    F = 12
+    f = np.linspace(0.5, 2.0, F)
+    kap = 0.9 * np.exp(-1.7j * f)
+    a = (1.0 + 0.3j * f) * 1e-3
+    V0, I0 = a, a / z0a
+    V1 = kap * a * np.sqrt(z0b / z0a)
+    I1_fwd = V1 / z0b
+    Vf = np.array([V0, V1])
+    If = np.array([I0, -I1_fwd])
+    S, Zr = post.sstar_uniform(Vf, If, [1, -1])
+    assert np.allclose(Zr[0], z0a, rtol=1e-14) and np.allclose(Zr[1], z0b, rtol=1e-14)
+    assert np.max(np.abs(S[:, 1, 0] - kap)) < 1e-14
+    assert np.max(np.abs(S[:, 0, 1] - kap)) < 1e-14
+    assert np.max(np.abs(S[:, 0, 0])) == 0.0 and np.max(np.abs(S[:, 1, 1])) == 0.0

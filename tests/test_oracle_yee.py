@@ -290,3 +290,116 @@ def test_two_run_protocol_is_reciprocal():
     # this boxed line), so |S11|^2 + |S21|^2 scatters by up to ~15% about 1.
     pw = np.abs(S[:, 0, 0]) ** 2 + np.abs(S[:, 1, 0]) ** 2
     assert np.max(np.abs(pw - 1.0)) < 0.25
+
+
+# ---------------------------------------------------------------- lossy media, port integrals
+
+@pytest.mark.parametrize("loss", [0.02, 30.0])
+def test_lossy_cavity_mode_follows_time_centred_conductor_recurrence(loss):
+    """Lossy dielectrics and metals (Sec. II-B, III; conductor reading: the conduction term
+    taken at the mean of the two time levels).  In a PEC cavity uniformly filled with eps and
+    sigma, one discrete mode (curl-curl eigenvalue lam) stays a mode.  With e_n its E^n
+    amplitude and g_n that of curl H^{n-1/2}, the leapfrog is exactly
+        g_{n+1} = g_n - (dt/mu0) lam e_n
+        eps (e_{n+1} - e_n)/dt + sigma (e_{n+1} + e_n)/2 = g_{n+1},
+    solved here for e_{n+1} from that discrete equation.  loss = sigma dt / (2 eps): 0.02 is
+    a lossy dielectric, 30 a metal whose E factor per step is negative (the Cu of the lossy
+    line sits near 125).  Any other conductor form (sigma dt/eps in place of sigma dt/2eps,
+    the exponential update) drifts from this recurrence by far more than roundoff."""
+    nx, ny, nz = 10, 8, 6
+    dx, dy, dz = 1.0e-3, 1.3e-3, 0.8e-3
+    eps_r = 2.0
+    courant = 0.95
+    dt = yee.courant_dt(dx, dy, dz, courant)
+    eps = yee.EPS0 * eps_r
+    sigma = 2.0 * loss * eps / dt
+    prob = _cavity(nx, ny, nz, dx, dy, dz, eps_r=eps_r, courant=courant)
+    prob.sigma = np.array([sigma])
+    m, n = 2, 3
+    K, J, I = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    shape = np.sin(m * math.pi * I / nx) * np.sin(n * math.pi * J / ny) * (K < nz)
+    lam = (2 / dx * math.sin(m * math.pi / (2 * nx))) ** 2 + \
+          (2 / dy * math.sin(n * math.pi / (2 * ny))) ** 2
+    f = np.zeros((6, nz + 1, ny + 1, nx + 1))
+    f[2] = shape
+    N = 200 if loss < 1 else 40
+    r = yee.run(prob, nsteps=N, fields_in=f, want_fields=True)
+    e, g = 1.0, 0.0
+    for _ in range(N):
+        g = g - dt / yee.MU0 * lam * e
+        e = ((eps / dt - sigma / 2.0) * e + g) / (eps / dt + sigma / 2.0)
+    out = r["fields"]
+    assert abs(e) > 1e-3                      # the mode has not simply died out
+    assert np.max(np.abs(out[2] - e * shape)) < 2e-12
+    assert np.max(np.abs(out[:2])) == 0.0
+    # per step the mode's two amplitudes shrink by the determinant of the recurrence,
+    # (eps/dt - sigma/2)/(eps/dt + sigma/2); for small loss that is exp(-sigma dt/eps), the
+    # continuous medium's energy decay
+    if loss < 1:
+        det = (eps / dt - sigma / 2.0) / (eps / dt + sigma / 2.0)
+        assert abs(math.log(det) + sigma * dt / eps) < (sigma * dt / eps) ** 3
+
+
+def _port_box(nx, ny, nz, dx, dy, dz, port):
+    prob = _cavity(nx, ny, nz, dx, dy, dz, eps_r=2.5, courant=0.9)
+    prob.ports = [port]
+    return prob
+
+
+def test_port_voltage_integrates_a_linear_ez_profile_exactly():
+    """Eq. 4, first line (reading: V = -(1/w) * surface sum of E_z dy dz with trapezoid
+    weights across the strip).  An E_z that is linear in y across the strip and varies along
+    z integrates exactly under the trapezoid rule:  with w = (j1 - j0) dy,
+        V = -dz * sum_{k0 <= k < k1} (E0 + r k),
+    whatever the slope s in y.  In a PEC cavity such a field is still in place after one
+    step at every edge two or more cells from the walls, where the port sits.  Dropping the
+    half weights, shifting the j range or the sign breaks the identity."""
+    nx, ny, nz = 12, 14, 10
+    dx, dy, dz = 1.0e-3, 0.7e-3, 1.2e-3
+    j0, j1, k0, k1 = 4, 9, 3, 7
+    port = W.Port(plane=6, direction=1, j0=j0, j1=j1, k0=k0, k1=k1, kb=k1, kt=k1, margin=1)
+    prob = _port_box(nx, ny, nz, dx, dy, dz, port)
+    E0, s, rz = 3.0, 0.75, -0.4
+    K, J, I = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    f = np.zeros((6, nz + 1, ny + 1, nx + 1))
+    f[2] = E0 + s * (J - 0.5 * (j0 + j1)) + rz * K
+    r = yee.run(prob, nsteps=1, fields_in=f, want_fields=True)
+    # the field on the V surface is unchanged by the step (it is linear there)
+    surf = np.s_[k0:k1, j0:j1 + 1, port.plane]
+    assert np.array_equal(r["fields"][2][surf], f[2][surf])
+    want = -dz * sum(E0 + rz * k for k in range(k0, k1))
+    assert abs(r["V"][0, 0] - want) < 1e-13 * abs(want)
+    # a uniform E_z gives V = -E_z h exactly, h = (k1 - k0) dz
+    f[2] = E0
+    r = yee.run(prob, nsteps=1, fields_in=f)
+    assert abs(r["V"][0, 0] + E0 * (k1 - k0) * dz) < 1e-13 * E0 * (k1 - k0) * dz
+
+
+@pytest.mark.parametrize("margin,direction", [(1, 1), (2, -1)])
+def test_loop_current_obeys_discrete_ampere_law(margin, direction):
+    """Eq. 4, second line (the closed H loop around the conductor).  By the discrete Stokes
+    theorem on the Yee grid, the loop sum of H.dl on the dual-grid rectangle in the plane
+    x = i + 1/2 equals the flux of curl H through it, and in a lossless medium the E update
+    turns that flux into  sum eps (E_x^{n+1} - E_x^n)/dt dy dz  over the E_x edges the loop
+    encloses.  With random fields and no conductor inside the loop, the port current after
+    one step (direction x the mean of the loops at plane -/+ 1/2) must equal that sum: any
+    wrong corner index, segment sign, orientation or dy/dz weight breaks it."""
+    nx, ny, nz = 12, 14, 12
+    dx, dy, dz = 1.0e-3, 0.7e-3, 1.2e-3
+    j0, j1, kb, kt = 5, 8, 5, 6
+    port = W.Port(plane=6, direction=direction, j0=j0, j1=j1, k0=0, k1=kb, kb=kb, kt=kt,
+                  margin=margin)
+    prob = _port_box(nx, ny, nz, dx, dy, dz, port)
+    dt = yee.courant_dt(dx, dy, dz, prob.courant)
+    f = W.random_fields((nz + 1, ny + 1, nx + 1), seed=23)
+    r = yee.run(prob, nsteps=1, fields_in=f, want_fields=True)
+    dEx = r["fields"][0] - f[0]
+    eps = yee.EPS0 * 2.5
+    enc = np.s_[kb - margin + 1:kt + margin, j0 - margin + 1:j1 + margin]   # enclosed (k, j)
+
+    def flux(i):
+        return np.sum(eps * dEx[enc + (i,)] / dt) * dy * dz
+
+    want = direction * 0.5 * (flux(port.plane - 1) + flux(port.plane))
+    assert abs(want) > 1e-3 * np.max(np.abs(f[3:])) * dy          # a sizeable current
+    assert abs(r["I"][0, 0] - want) < 1e-12 * np.max(np.abs(f[3:])) * (ny * dy + nz * dz)
