@@ -75,6 +75,16 @@ def _load():
         _lib.oracle_run.argtypes = [C.POINTER(_Problem), C.c_long, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        _lib.oracle_open.restype = C.c_void_p
+        _lib.oracle_open.argtypes = [C.POINTER(_Problem)]
+        _lib.oracle_advance.restype = C.c_int
+        _lib.oracle_advance.argtypes = [C.c_void_p, C.POINTER(_Problem), C.c_long,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]
+        _lib.oracle_close.restype = None
+        _lib.oracle_close.argtypes = [C.c_void_p]
+        _lib.oracle_set_threads.restype = None
+        _lib.oracle_set_threads.argtypes = [C.c_int]
         _lib.oracle_waveform.restype = C.c_double
         _lib.oracle_waveform.argtypes = [C.POINTER(_Problem), C.c_long]
     return _lib
@@ -147,8 +157,7 @@ def run(prob, nsteps: Optional[int] = None, dt: Optional[float] = None, fields_i
         want_fields: bool = False, want_energy: bool = False, threads: Optional[int] = None):
     """Run the oracle.  Returns dict(V, I, dt, fields (6,nz+1,ny+1,nx+1) or None, energy)."""
     lib = _load()
-    if threads is not None:
-        os.environ["OMP_NUM_THREADS"] = str(threads)
+    lib.oracle_set_threads(int(threads) if threads is not None else (os.cpu_count() or 1))
     n = prob.nsteps if nsteps is None else nsteps
     if dt is None:
         dt = courant_dt(prob.dx, prob.dy, prob.dz, prob.courant)
@@ -173,6 +182,48 @@ def run(prob, nsteps: Optional[int] = None, dt: Optional[float] = None, fields_i
     return dict(V=V[:len(prob.ports), :n], I=I[:len(prob.ports), :n], dt=dt,
                 fields=fout.reshape(shp) if fout is not None else None,
                 energy=en[:n] if en is not None else None)
+
+
+class Stepper:
+    """The oracle held open between calls: set-up once (zero fields), then `advance(n)`
+    runs the next n steps and returns the seconds those steps alone took (allocation and
+    the coefficient / CPML set-up are outside every timer); their port samples are left in
+    `V` and `I`.  For timing the oracle's stepping rate; `close()` frees its memory."""
+
+    def __init__(self, prob, threads: Optional[int] = None):
+        self.lib = _load()
+        self.lib.oracle_set_threads(int(threads) if threads is not None else (os.cpu_count() or 1))
+        self.prob = prob
+        self.dt = courant_dt(prob.dx, prob.dy, prob.dz, prob.courant)
+        self.s, self.keep = _make(prob, self.dt)
+        self.h = self.lib.oracle_open(C.byref(self.s))
+        if not self.h:
+            raise MemoryError("oracle_open failed to allocate")
+
+    def advance(self, nsteps: int, threads: Optional[int] = None) -> float:
+        if threads is not None:
+            self.lib.oracle_set_threads(int(threads))
+        np_ = max(len(self.prob.ports), 1)
+        V = np.zeros((np_, max(nsteps, 1)))
+        I = np.zeros((np_, max(nsteps, 1)))
+        sec = C.c_double(0.0)
+        rc = self.lib.oracle_advance(self.h, C.byref(self.s), nsteps, _ptr(V, C.c_double),
+                                     _ptr(I, C.c_double), C.byref(sec))
+        if rc != 0:
+            raise MemoryError("oracle_advance failed to allocate")
+        self.V, self.I = V[:len(self.prob.ports), :nsteps], I[:len(self.prob.ports), :nsteps]
+        return sec.value
+
+    def close(self):
+        if self.h:
+            self.lib.oracle_close(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def waveform_samples(prob, nsteps: int, dt: Optional[float] = None) -> np.ndarray:

@@ -43,6 +43,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+#include <omp.h>
 
 /* CODATA 2018 vacuum constants (SI). */
 #define OR_C0   299792458.0
@@ -462,20 +464,20 @@ static void free_state(oracle_state *s)
     }
 }
 
-/*
- * Run nsteps of the time loop.
- *   V, I       : nports*nsteps outputs (port-major), may be NULL when nports == 0
- *   fields_in  : optional 6 arrays (ex,ey,ez,hx,hy,hz) of (nz+1)(ny+1)(nx+1): E^0, H^{-1/2}
- *   fields_out : optional 6 arrays of the same shape: E^N, H^{N-1/2}
- *   energy     : optional nsteps values of W^n, n = 0..nsteps-1
- * Returns 0 on success, -1 on allocation failure.
- */
-int oracle_run(const oracle_problem *p, long nsteps, double *V, double *I,
-               const double *fields_in, double *fields_out, double *energy)
+static void record_ports(const oracle_problem *p, const oracle_state *s, long n, long nsteps,
+                         double *V, double *I)
 {
-    oracle_state st;
-    memset(&st, 0, sizeof(st));
-    oracle_state *s = &st;
+    for (int t = 0; t < p->nports; ++t) {
+        V[(long)t * nsteps + n] = port_voltage(p, s, t);
+        I[(long)t * nsteps + n] = port_current(p, s, t);
+    }
+}
+
+/* Allocate the state, derive the edge coefficients and CPML profiles, load the initial
+ * fields.  Returns 0, or -1 on allocation failure (nothing left allocated). */
+static int setup_state(const oracle_problem *p, const double *fields_in, oracle_state *s)
+{
+    memset(s, 0, sizeof(*s));
     s->nx = p->nx; s->ny = p->ny; s->nz = p->nz;
     s->n = (long)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
     double **d[] = {&s->ex, &s->ey, &s->ez, &s->hx, &s->hy, &s->hz, &s->ca_x, &s->cb_x, &s->ca_y,
@@ -502,12 +504,20 @@ int oracle_run(const oracle_problem *p, long nsteps, double *V, double *I,
                 f[c][q] = live ? fields_in[(long)c * s->n + q] : 0.0;
             }
     }
+    return 0;
+}
+
+/* Steps n0 .. n0+nsteps-1 of the time loop (see the order at the top of this file); the
+ * port samples of step n go to V, I at column n - n0 of rows of length nsteps. */
+static int time_loop(const oracle_problem *p, oracle_state *s, long n0, long nsteps, double *V,
+                     double *I, double *energy)
+{
     double *hprev = NULL;
     if (energy) {
         hprev = malloc(3 * s->n * sizeof(double));
-        if (!hprev) { free_state(s); return -1; }
+        if (!hprev) return -1;
     }
-    for (long n = 0; n < nsteps; ++n) {
+    for (long n = n0; n < n0 + nsteps; ++n) {
         double we = 0.0;
         if (energy) {
             we = energy_e(p, s);
@@ -523,7 +533,7 @@ int oracle_run(const oracle_problem *p, long nsteps, double *V, double *I,
                 if (s->db_y[q] > 0.0) wh += (p->dt / s->db_y[q]) * hprev[s->n + q] * s->hy[q];
                 if (s->db_z[q] > 0.0) wh += (p->dt / s->db_z[q]) * hprev[2 * s->n + q] * s->hz[q];
             }
-            energy[n] = we + wh;
+            energy[n - n0] = we + wh;
         }
         update_e(p, s);
         if (p->src_kind != OR_WAVE_NONE) {
@@ -534,18 +544,86 @@ int oracle_run(const oracle_problem *p, long nsteps, double *V, double *I,
                     if (!s->pec_z[q]) s->ez[q] += a;
                 }
         }
-        for (int t = 0; t < p->nports; ++t) {
-            V[(long)t * nsteps + n] = port_voltage(p, s, t);
-            I[(long)t * nsteps + n] = port_current(p, s, t);
-        }
-    }
-    if (fields_out) {
-        double *f[6] = {s->ex, s->ey, s->ez, s->hx, s->hy, s->hz};
-        for (int c = 0; c < 6; ++c) memcpy(fields_out + (long)c * s->n, f[c], s->n * sizeof(double));
+        record_ports(p, s, n - n0, nsteps, V, I);
     }
     free(hprev);
-    free_state(s);
     return 0;
+}
+
+static void copy_fields_out(const oracle_state *s, double *fields_out)
+{
+    const double *f[6] = {s->ex, s->ey, s->ez, s->hx, s->hy, s->hz};
+    for (int c = 0; c < 6; ++c) memcpy(fields_out + (long)c * s->n, f[c], s->n * sizeof(double));
+}
+
+/*
+ * Run nsteps of the time loop.
+ *   V, I       : nports*nsteps outputs (port-major), may be NULL when nports == 0
+ *   fields_in  : optional 6 arrays (ex,ey,ez,hx,hy,hz) of (nz+1)(ny+1)(nx+1): E^0, H^{-1/2}
+ *   fields_out : optional 6 arrays of the same shape: E^N, H^{N-1/2}
+ *   energy     : optional nsteps values of W^n, n = 0..nsteps-1
+ * Returns 0 on success, -1 on allocation failure.
+ */
+int oracle_run(const oracle_problem *p, long nsteps, double *V, double *I,
+               const double *fields_in, double *fields_out, double *energy)
+{
+    oracle_state st;
+    if (setup_state(p, fields_in, &st) != 0) return -1;
+    int rc = time_loop(p, &st, 0, nsteps, V, I, energy);
+    if (rc == 0 && fields_out) copy_fields_out(&st, fields_out);
+    free_state(&st);
+    return rc;
+}
+
+/*
+ * A run held open between calls, for timing the stepping alone:
+ *   oracle_open    allocates the state and does the set-up (coefficients, CPML
+ *                  profiles), fields at zero; NULL on allocation failure;
+ *   oracle_advance runs the next nsteps steps (the source clock continues from the
+ *                  steps already taken), port samples into V, I (nports rows of
+ *                  nsteps), and puts the wall-clock seconds of those steps alone in
+ *                  *seconds; returns 0, or -1 on allocation failure;
+ *   oracle_close   frees the state.
+ * The problem must outlive the handle.
+ */
+typedef struct {
+    oracle_state st;
+    long steps_done;
+} oracle_handle;
+
+oracle_handle *oracle_open(const oracle_problem *p)
+{
+    oracle_handle *h = calloc(1, sizeof(oracle_handle));
+    if (!h) return NULL;
+    if (setup_state(p, NULL, &h->st) != 0) { free(h); return NULL; }
+    return h;
+}
+
+int oracle_advance(oracle_handle *h, const oracle_problem *p, long nsteps, double *V, double *I,
+                   double *seconds)
+{
+    struct timespec t0, t1;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
+    int rc = time_loop(p, &h->st, h->steps_done, nsteps, V, I, NULL);
+    clock_gettime(CLOCK_MONOTONIC, &t1);
+    if (seconds)
+        *seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+    if (rc == 0) h->steps_done += nsteps;
+    return rc;
+}
+
+void oracle_close(oracle_handle *h)
+{
+    if (!h) return;
+    free_state(&h->st);
+    free(h);
+}
+
+/* Threads of the OpenMP loops over k-planes for the following runs (the environment
+ * variable is read once, when the OpenMP runtime starts). */
+void oracle_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
 }
 
 /* The waveform as the oracle evaluates it, for the closed-form DFT pins. */

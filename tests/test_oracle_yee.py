@@ -403,3 +403,19 @@ def test_loop_current_obeys_discrete_ampere_law(margin, direction):
     want = direction * 0.5 * (flux(port.plane - 1) + flux(port.plane))
     assert abs(want) > 1e-3 * np.max(np.abs(f[3:])) * dy          # a sizeable current
     assert abs(r["I"][0, 0] - want) < 1e-12 * np.max(np.abs(f[3:])) * (ny * dy + nz * dz)
+
+
+def test_stepper_continues_the_run_exactly():
+    """The held-open oracle (used to time the stepping alone) advances the same run: 120 +
+    180 steps give the port histories of one 300-step run bit for bit (the source clock
+    continues across calls)."""
+    p = W.config_small_fp64()
+    ref = yee.run(p, nsteps=300)
+    with yee.Stepper(p, threads=2) as st:
+        st.advance(120)
+        V0, I0 = st.V.copy(), st.I.copy()
+        sec = st.advance(180)
+        V1, I1 = st.V, st.I
+    assert sec > 0.0
+    assert np.array_equal(np.concatenate([V0, V1], axis=1), ref["V"])
+    assert np.array_equal(np.concatenate([I0, I1], axis=1), ref["I"])
