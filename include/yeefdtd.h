@@ -245,8 +245,13 @@ yf_status yf_sparams(int nports, int nfreq, const double *freqs, const yf_port_d
  *     held from library load until process exit: nfreq * nports^2 <= 32768 complex entries
  *     (512 KiB); larger requests return YF_E_INVALID before any work is queued.
  *   - asynchronous on `stream` (NULL = legacy default stream); the caller synchronises.
- *   - the first call on each device looks up the scratch address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *   - every call made while `stream` is not capturing looks up the scratch's device address
+ *     (cudaGetSymbolAddress) in the current context and records it; a call made while
+ *     `stream` is capturing uses the recorded address.  So the first call in each context
+ *     (each device, and again after anything that destroys the context, such as
+ *     cudaDeviceReset) must come before any stream capture; otherwise YF_E_STATE.
+ *   - an error already pending in the CUDA runtime is returned (and cleared) before any work
+ *     is queued; an error after that names the launch that failed.
  *   - every call shares the one scratch array and overwrites all of it that it uses: calls
  *     that may overlap on the GPU (different streams, concurrent host threads) race; order
  *     them on one stream or synchronise between them. */

@@ -412,6 +412,7 @@ extern "C" yf_status yf_rlcg(int nfreq, const double *freqs, const double *S_sta
 // matrix S* that the phase-delay pass reads back, lives in a fixed device array instead of
 // a per-call cudaMalloc, and the caller provides every input and output on the device.
 
+#include <cudaTypedefs.h>
 #include <mutex>
 
 namespace yf {
@@ -425,25 +426,61 @@ constexpr int kNoAllocMaxDevices = 64;
 // memory.  The device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) cplx g_noalloc_sstar[kNoAllocMaxEntries];
 
+// The device address of the array as last looked up on each device, with the context it
+// was looked up in: a context that is destroyed and created again (cudaDeviceReset) loads
+// the module afresh, and the array may then sit elsewhere.
+struct NoAllocAddr {
+    CUcontext ctx;
+    cplx *ptr;
+};
 std::mutex g_noalloc_mu;
-cplx *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// Once per device, with that device current: look up the array's device address.
-yf_status noalloc_scratch(cplx **out)
+yf_status current_context(CUcontext *ctx)
+{
+    static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+    if (!get) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(YF_E_CUDA, "yf_sparams_noalloc: cuCtxGetCurrent is not available");
+        get = (PFN_cuCtxGetCurrent_v4000)fn;
+    }
+    if (get(ctx) != CUDA_SUCCESS || !*ctx)
+        return fail(YF_E_CUDA, "yf_sparams_noalloc: no current CUDA context");
+    return YF_OK;
+}
+
+// The array's device address in the current context.  A call outside stream capture looks
+// it up (cheap once the module is loaded) and records it with the context; a call while
+// `s` is capturing uses the recorded address, which must come from the same context.
+yf_status noalloc_scratch(cudaStream_t s, cplx **out)
 {
     int dev = -1;
     YF_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(YF_E_UNSUPPORTED, "yf_sparams_noalloc: device %d beyond the %d supported", dev,
                     kNoAllocMaxDevices);
+    CUcontext ctx = nullptr;
+    yf_status st = current_context(&ctx);
+    if (st != YF_OK) return st;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    YF_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocAddr &a = g_noalloc_addr[dev];
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sstar);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_sstar)");
-        g_noalloc_ptr[dev] = (cplx *)p;
+        a.ctx = ctx;
+        a.ptr = (cplx *)p;
+    } else if (!a.ptr || a.ctx != ctx) {
+        return fail(YF_E_STATE, "yf_sparams_noalloc: the first call in a CUDA context (device %d) "
+                                "must come before any stream capture", dev);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = a.ptr;
     return YF_OK;
 }
 
@@ -467,10 +504,13 @@ extern "C" yf_status yf_sparams_noalloc(int nports, int nfreq, const double *fre
         return fail(YF_E_INVALID,
                     "yf_sparams_noalloc: nfreq * nports^2 = %ld exceeds the fixed scratch of %d entries",
                     entries, kNoAllocMaxEntries);
-    cplx *scratch = nullptr;
-    yf_status st = noalloc_scratch(&scratch);
-    if (st != YF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // an error left by earlier, unrelated work is reported before anything is queued, so a
+    // failure here always means that this call wrote none of its outputs
+    YF_CUDA_TRY(cudaGetLastError());
+    cplx *scratch = nullptr;
+    yf_status st = noalloc_scratch(s, &scratch);
+    if (st != YF_OK) return st;
     SpArgs A;
     A.n = nports; A.nf = nfreq; A.uniform = 0; A.dir1 = 1; A.z_ref = z_ref;
     A.vinc = (const cplx *)V_inc;
@@ -481,8 +521,14 @@ extern "C" yf_status yf_sparams_noalloc(int nports, int nfreq, const double *fre
     A.zr = (cplx *)Zr;
     A.zc = (nports == 2) ? (cplx *)Zc : nullptr;
     k_sparams<<<(nfreq + 63) / 64, 64, 0, s>>>(A);
-    if (tau) k_phase_delay<<<1, 64, 0, s>>>(scratch, freqs, nports, nfreq, tau);
-    YF_CUDA_TRY(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "yf_sparams_noalloc: k_sparams launch");
+    if (tau) {
+        k_phase_delay<<<1, 64, 0, s>>>(scratch, freqs, nports, nfreq, tau);
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return cuda_fail(e, "yf_sparams_noalloc: k_phase_delay launch (S, Zr, Zc queued)");
+    }
     if (S_star)
         YF_CUDA_TRY(cudaMemcpyAsync(S_star, scratch, (size_t)entries * sizeof(cplx),
                                     cudaMemcpyDeviceToDevice, s));

@@ -13,9 +13,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--ref-seconds", "2"], cwd=ROOT, capture_output=True,
-                         text=True, timeout=600)
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--ref-seconds", "1", "--oracle-slice"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -27,6 +27,12 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the line names what was timed: the slice's cells, the oracle steps of one bench step,
+    # and a per-step time that is the measured one (cells x steps / rate)
+    assert d["config"]["cells"] == 256 * 128 * 256 and "256x128x256" in d["config"]["workload"]
+    per = d["config"]["cells"] * d["config"]["steps_per_bench_step"] / (d["value"] * 1e9)
+    assert abs(d["ms_per_step"] / 1e3 - per) <= 1e-6 * per
+    assert "set-up outside the timer" in d["cpu_baseline"]["sample"]
 
 
 def test_stored_traffic_is_dropped_when_the_stencil_changes(tmp_path, monkeypatch):

@@ -1,9 +1,11 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
 
-Tolerances (written here, derived in the design doc):
-  FP64 fields      relative L2 over all six components <= 1e-12 after 2000 steps
+Tolerances:
+  FP64 fields      relative L2 over all six components <= 1e-12 after 2000 steps (the
+                   two sides differ only in the rounding order of the same FP64 operations)
   FP64 port DFTs   relative (to the spectrum's max)    <= 1e-10
-  FP32 fields      relative L2                         <= 1e-5
+  FP32 fields      relative L2                         <= 1e-5 (unit roundoff 6e-8 times the
+                   steps the error has grown over, with a margin)
   FP32 |S_ij|      absolute                            <= 1e-3
 """
 import math

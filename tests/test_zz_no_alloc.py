@@ -6,7 +6,8 @@ global-mode stream capture, or programs whose device memory belongs to their own
 they pass device buffers for every input and output, and the library keeps its one
 intermediate in a fixed per-GPU array.  Here torch, acting as such a caller, owns all
 buffers; two calls in a row with different port counts and frequency grids must both
-reproduce the allocating entry point within the extraction tests' tolerance.
+reproduce the allocating entry point within the extraction tests' tolerance, also when
+the call is captured into a CUDA graph in global mode and replayed on new inputs.
 """
 import numpy as np
 import pytest
@@ -68,6 +69,55 @@ def test_noalloc_extraction_matches_allocating_entry_point(gpu):
             assert _close(got[key], ref[key]), key
         if N == 2:
             assert _close(got["Zc"], ref["Zc"])
+
+
+def test_noalloc_extraction_skips_optional_outputs(gpu):
+    """S_star and tau (and Zc of a 2-port) are optional: passing None leaves S and Zr as the
+    allocating entry point gives them."""
+    import torch
+    freqs, Vi, Ii, Vt = _spectra(13, 2, 48)
+    ref = gpu.sparams(freqs, Vi, Ii, Vt)
+    S = torch.zeros((48, 2, 2, 2), dtype=torch.float64, device="cuda")
+    Zr = torch.zeros((2, 48, 2), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    gpu.sparams_noalloc(2, 48, _dev(freqs), _dev(Vi), _dev(Ii), _dev(Vt), S, Zr,
+                        stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert _close(_cplx(S), ref["S"]) and _close(_cplx(Zr), ref["Zr"])
+
+
+def test_noalloc_extraction_inside_a_captured_graph(gpu):
+    """The reason the entry point exists: it can be enqueued while a stream is captured in
+    global mode, where allocating is illegal.  One call is captured into a CUDA graph after
+    an eager call on the same device; the graph is then replayed on new spectra copied into
+    the same input buffers, twice, and each replay matches the allocating entry point."""
+    import torch
+    N, F = 3, 40
+    freqs, Vi, Ii, Vt = _spectra(21, N, F)
+    bufs = [_dev(freqs), _dev(Vi), _dev(Ii), _dev(Vt)]
+    S = torch.zeros((F, N, N, 2), dtype=torch.float64, device="cuda")
+    Ss = torch.zeros_like(S)
+    Zr = torch.zeros((N, F, 2), dtype=torch.float64, device="cuda")
+    tau = torch.zeros((F, N, N), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        gpu.sparams_noalloc(N, F, *bufs, S, Zr, S_star=Ss, tau=tau, stream=side.cuda_stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        cap = torch.cuda.current_stream()
+        gpu.sparams_noalloc(N, F, *bufs, S, Zr, S_star=Ss, tau=tau, stream=cap.cuda_stream)
+    for seed in (22, 23):
+        freqs, Vi, Ii, Vt = _spectra(seed, N, F)
+        for b, new in zip(bufs, (freqs, Vi, Ii, Vt)):
+            b.copy_(_dev(new))
+        S.zero_(); Ss.zero_(); Zr.zero_(); tau.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = gpu.sparams(freqs, Vi, Ii, Vt)
+        got = dict(S=_cplx(S), S_star=_cplx(Ss), Zr=_cplx(Zr), tau=tau.cpu().numpy())
+        for key in ("S_star", "S", "Zr", "tau"):
+            assert _close(got[key], ref[key]), (seed, key)
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(gpu):
