@@ -186,7 +186,8 @@ void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, co
 // E^{n+1}, H^{n+1/2}.  The box [bx0, bx1] x [by0, by1] x [bz0, bz1] is a union of 32 x 8 tiles.
 // tile and TMA boxes of the two-step kernel
 constexpr int kTbTileX = 32, kTbTileY = 8;   // output tile
-constexpr int kTbWinX = 40, kTbWinY = 12;    // E and H windows: x from i0-4, y from j0-2
+constexpr int kTbWinX = 40, kTbWinY = 12;    // E windows: x from i0-4, y from j0-2
+constexpr int kTbWinHY = 11;                 // H windows: the same x and first row, 11 rows
 constexpr int kTbClsX = 80, kTbClsY = 10;    // class tiles: x from i0-16, y from j0-1
 struct TbArgs {
     int px;

@@ -182,10 +182,11 @@ yf_status tb_build(yf_grid *g)
 
     // two-step arguments and maps by source buffer r: B = buf[r+1], C = buf[r+2]
     TbArgs ta[3];
-    CUtensorMap tm[6];
+    CUtensorMap tm[9];
     const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
     const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
     const cuuint32_t wbox[4] = {kTbWinX, kTbWinY, 1, 3};
+    const cuuint32_t hbox[4] = {kTbWinX, kTbWinHY, 1, 3};
     const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
     const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
     const cuuint32_t cbox[4] = {kTbClsX, kTbClsY, 1, 3};
@@ -203,11 +204,16 @@ yf_status tb_build(yf_grid *g)
         a.B = (float *)g->buf[(r + 1) % 3];
         a.C = (float *)g->buf[(r + 2) % 3];
         a.bx0 = B[0]; a.bx1 = B[1]; a.by0 = B[2]; a.by1 = B[3]; a.bz0 = B[4]; a.bz1 = B[5];
-        CUresult cr = encode(&tm[2 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
+        // per source buffer: the E window map, the H window map, the class-tile map
+        CUresult cr = encode(&tm[3 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr == CUDA_SUCCESS)
-            cr = encode(&tm[2 * r + 1], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
+            cr = encode(&tm[3 * r + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, hbox, one,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr == CUDA_SUCCESS)
+            cr = encode(&tm[3 * r + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return bail(fail(YF_E_CUDA, "variant 4: tensor map encoding failed (%d)", (int)cr));
