@@ -172,11 +172,19 @@ yf_status yf_set_dft_mode(yf_grid *g, int mask);
  *      rest of the grid one step at a time, with the port epilogue after each step.  Uses a
  *      third field buffer (6 (nz+1)(ny+1) px words more, px = nx+1 rounded up to 32, allocated here or at the first step and
  *      freed when another variant is set).  An odd remaining step runs as variant 2.  The
- *      two-step blocks take min(64, 2 kseg) z-planes each.
+ *      two-step blocks take 2 kseg z-planes each unless yf_set_box_segment says otherwise.
  * tile_y in {4, 8, 16}, 1 <= kseg <= 64.  All variants compute the same update; results agree to
  * rounding.  Drops captured graphs; may be called between steps.  YF_E_INVALID for variant 4
  * on an FP64 grid or on one with 6 (nz+1)(ny+1) px >= 2^31 (32-bit offsets in its kernel). */
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg);
+
+/* Variant 4: z-planes per block of the two-step kernel (planes >= 1), or 0 for the default
+ * 2 kseg.  A tuning choice only: every segmentation gives the same fields bit for bit (each
+ * block recomputes its halo planes from step-n data).  Longer segments re-read fewer halo
+ * planes; the count of blocks decides how they pack onto the SMs and how much of the frame's
+ * first step runs beside them.  Drops captured graphs; may be called between steps.
+ * YF_E_INVALID for planes < 0. */
+yf_status yf_set_box_segment(yf_grid *g, int planes);
 
 /* Variant 4's inner box as node ranges x0, x1, y0, y1, z0, z1 (inclusive; all -1 when the
  * grid has no box, which then steps one step at a time).  Finalises the geometry like a first

@@ -1155,6 +1155,20 @@ yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
     return YF_OK;
 }
 
+yf_status yf_set_box_segment(yf_grid *g, int planes)
+{
+    if (!g) return fail(YF_E_INVALID, "yf_set_box_segment: NULL grid");
+    if (planes < 0) return fail(YF_E_INVALID, "yf_set_box_segment: planes must be >= 0");
+    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    for (int b = 0; b < 6; ++b)
+        if (g->graph[b]) { cudaGraphExecDestroy(g->graph[b]); g->graph[b] = nullptr; }
+    const bool had_tb = g->tb != nullptr;
+    if (had_tb) tb_free(g);
+    g->box_seg = planes;
+    if (had_tb) return tb_build(g);
+    return YF_OK;
+}
+
 // checkpoint: header, fields, CPML auxiliaries, accumulators, counters
 struct CkptHeader {
     char magic[8];

@@ -141,9 +141,10 @@ yf_status tb_build(yf_grid *g)
             if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
             if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
         }
-    // z-planes per two-step block: twice the one-step segment (the two-step block re-reads four
-    // halo planes instead of two), at most the one-step kernels' limit
-    const int seg = std::min(kMaxKseg, 2 * g->kseg);
+    // z-planes per two-step block: as set by yf_set_box_segment, else twice the one-step
+    // segment (the two-step block re-reads four halo planes instead of two); its rings are
+    // indexed modulo their depth, so any length works
+    const int seg = g->box_seg > 0 ? g->box_seg : 2 * g->kseg;
     if (have_box)
         for (int kb = B[4]; kb <= B[5]; kb += seg)
             for (int j0 = B[2]; j0 <= B[3]; j0 += kTbTileY)

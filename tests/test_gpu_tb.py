@@ -130,6 +130,34 @@ def test_graph_chunks_equal_direct_pairs(gpu):
         assert np.array_equal(a.port_dfts()[0], b.port_dfts()[0])
 
 
+@pytest.mark.parametrize("box_seg", [3, 14, 37])
+def test_box_segmentation_does_not_change_the_fields(gpu, box_seg):
+    """The box's 37 planes cut into segments of 3 (the shortest the rings allow, thirteen
+    segments), 14 (a ragged last segment of 9) or 37 (one segment), against the default
+    (32 planes, then 5): each block recomputes its halo planes from step-n data, so the
+    fields and spectra agree bit for bit, also after the segmentation changes mid-run."""
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as a, \
+            gpu.Grid(p, prec=gpu.FP32, variant=4, box_seg=box_seg) as b:
+        a.step(40)
+        b.step(40)
+        assert np.array_equal(a.fields(), b.fields())
+        gpu.set_box_segment(b.h, 0)
+        a.step(21)
+        b.step(21)
+        assert np.array_equal(a.fields(), b.fields())
+        assert np.array_equal(a.port_dfts()[0], b.port_dfts()[0])
+        assert np.array_equal(a.port_dfts()[1], b.port_dfts()[1])
+
+
+def test_box_segment_rejects_negative(gpu):
+    p = _tb_problem()
+    with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
+        with pytest.raises(gpu.YFError) as e:
+            gpu.set_box_segment(g.h, -1)
+        assert e.value.code == gpu.E_INVALID
+
+
 def test_launch_count(gpu):
     p = _tb_problem()
     with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
