@@ -283,7 +283,7 @@ EpiParams<T> epi_params(const yf_grid *g)
     E.ports = g->ports_dev; E.inc = g->inc_dev; E.dft_mask = g->dft_mask;
     E.acc64 = g->acc64; E.acc32 = g->acc32; E.kahan = g->kahan;
     E.dy = g->dy; E.dz = g->dz;
-    E.ctr = g->ctr; E.status = g->status;
+    E.ctr = g->ctr; E.src_ctr = g->ctr + 1; E.skip_source = 0; E.status = g->status;
     return E;
 }
 
@@ -404,8 +404,9 @@ yf_status finalize(yf_grid *g)
         YF_CUDA_TRY(cudaMemcpy(g->segs_dev, g->segs.data(), nseg * sizeof(EpiSeg), cudaMemcpyHostToDevice));
         YF_CUDA_TRY(cudaMalloc(&g->slots, nseg * sizeof(double)));
     }
-    YF_CUDA_TRY(cudaMalloc(&g->ticket, sizeof(unsigned int)));
-    YF_CUDA_TRY(cudaMemset(g->ticket, 0, sizeof(unsigned int)));
+    // [0] the epilogue's blocks, [1] the source kernel's (the two may run on different streams)
+    YF_CUDA_TRY(cudaMalloc(&g->ticket, 2 * sizeof(unsigned int)));
+    YF_CUDA_TRY(cudaMemset(g->ticket, 0, 2 * sizeof(unsigned int)));
     if (g->variant >= 2) {
         st = encode_maps(g);
         if (st != YF_OK) return st;
@@ -466,7 +467,7 @@ yf_status reset_state(yf_grid *g)
         YF_CUDA_TRY(cudaMemsetAsync(g->acc32, 0, (size_t)g->nf_total * 4 * sizeof(float), g->stream));
         YF_CUDA_TRY(cudaMemsetAsync(g->kahan, 0, (size_t)g->nf_total * 8 * sizeof(float), g->stream));
     }
-    YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(long long), g->stream));
+    YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, 2 * sizeof(long long), g->stream));
     YF_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), g->stream));
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     g->steps_done = 0;
@@ -490,9 +491,10 @@ static yf_status capture_chunk(yf_grid *g)
     tb_unchain(g);
     YF_CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (g->variant == 4)
+    if (g->variant == 4) {
         for (int t = 0; t + 1 < g->chunk && e == cudaSuccess; t += 2) e = tb_pair(g, g->stream);
-    else
+        if (e == cudaSuccess) e = tb_join(g, g->stream);   // every forked stream rejoins the capture
+    } else
         for (int t = 0; t < g->chunk && e == cudaSuccess; ++t) e = step_direct(g, g->stream);
     cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
     // capture only records: the state advances when the graph is launched
@@ -570,8 +572,9 @@ yf_status yf_grid_create(int nx, int ny, int nz, double dx, double dy, double dz
     for (int c = 0; c < 3; ++c) g->cls[c] = g->cls_base + c * g->npts;
     if ((e = cudaMalloc(&g->ctab, 2 * kMaxClasses * g->esz)) != cudaSuccess) return bail(e, "cudaMalloc ctab");
     if ((e = cudaMalloc(&g->eps_tab, kMaxClasses * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc eps");
-    if ((e = cudaMalloc(&g->ctr, sizeof(long long))) != cudaSuccess) return bail(e, "cudaMalloc ctr");
-    if ((e = cudaMemset(g->ctr, 0, sizeof(long long))) != cudaSuccess) return bail(e, "cudaMemset ctr");
+    // [0] steps whose port samples are transformed, [1] steps whose source is added
+    if ((e = cudaMalloc(&g->ctr, 2 * sizeof(long long))) != cudaSuccess) return bail(e, "cudaMalloc ctr");
+    if ((e = cudaMemset(g->ctr, 0, 2 * sizeof(long long))) != cudaSuccess) return bail(e, "cudaMemset ctr");
     if ((e = cudaMalloc(&g->status, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc status");
     if ((e = cudaMemset(g->status, 0, sizeof(int))) != cudaSuccess) return bail(e, "cudaMemset status");
     if ((e = cudaMalloc(&g->energy_partials, (kEnergyBlocks + 1) * sizeof(double))) != cudaSuccess)
@@ -790,6 +793,7 @@ yf_status yf_step(yf_grid *g, long n)
     if (g->variant == 4) {
         tb_unchain(g);   // the first direct pair forks after everything queued so far
         for (; done + 2 <= n; done += 2) YF_CUDA_TRY(tb_pair(g, g->stream));
+        YF_CUDA_TRY(tb_join(g, g->stream));
         tb_unchain(g);
     }
     for (; done < n; ++done) YF_CUDA_TRY(step_direct(g, g->stream));
@@ -1000,31 +1004,35 @@ static cudaError_t profile_one(yf_grid *g, cudaEvent_t *ev, int *nk)
 }
 
 // variant 4: pairs of steps; per launch the box kernel (one per pair), the first frame step
-// (beside the box kernel), the second frame step (after it) and the epilogue (two per pair)
+// (beside the box kernel), the second frame step (after it), the source (two per pair, on the
+// critical path) and the port integrals with the transforms (two per pair, side stream)
 static yf_status profile_tb(yf_grid *g, long n, double *ms, int *nkern)
 {
-    cudaEvent_t ev[8];
-    for (int q = 0; q < 8; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
+    cudaEvent_t ev[12];
+    for (int q = 0; q < 12; ++q) YF_CUDA_TRY(cudaEventCreate(&ev[q]));
     const long pairs = n < 2 ? 1 : n / 2;
-    double acc[4] = {0, 0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (long t = 0; t < pairs && e == cudaSuccess; ++t) {
         tb_unchain(g);   // each traced pair on its own
         e = tb_pair(g, g->stream, ev);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
-        float m[5] = {0, 0, 0, 0, 0};
-        const int from[5] = {0, 2, 3, 5, 6}, to[5] = {1, 3, 4, 6, 7};
-        for (int q = 0; q < 5 && e == cudaSuccess; ++q) e = cudaEventElapsedTime(&m[q], ev[from[q]], ev[to[q]]);
+        if (e == cudaSuccess) e = tb_join(g, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        float m[7] = {0, 0, 0, 0, 0, 0, 0};
+        const int from[7] = {0, 2, 3, 5, 6, 8, 10}, to[7] = {1, 3, 4, 6, 7, 9, 11};
+        for (int q = 0; q < 7 && e == cudaSuccess; ++q) e = cudaEventElapsedTime(&m[q], ev[from[q]], ev[to[q]]);
         acc[0] += m[0];
         acc[1] += m[1];
         acc[2] += m[3];
         acc[3] += 0.5 * (m[2] + m[4]);
+        acc[4] += 0.5 * (m[5] + m[6]);
     }
-    for (int q = 0; q < 8; ++q) cudaEventDestroy(ev[q]);
+    tb_unchain(g);
+    for (int q = 0; q < 12; ++q) cudaEventDestroy(ev[q]);
     YF_CUDA_TRY(e);
     g->steps_done += 2 * pairs;
-    for (int q = 0; q < 4; ++q) ms[q] = acc[q] / (double)pairs;
-    *nkern = 4;
+    for (int q = 0; q < 5; ++q) ms[q] = acc[q] / (double)pairs;
+    *nkern = 5;
     return YF_OK;
 }
 
@@ -1065,9 +1073,9 @@ const char *yf_kernel_name(yf_grid *g, int idx)
     static const char *tma[] = {"k_yee_tma_batch", "k_epilogue"};
     static const char *skew[] = {"k_yee_skew", "k_epilogue"};
     static const char *tb[] = {"k_yee_tb2", "k_yee_tma_batch (frame step 1)", "k_yee_tma_batch (frame step 2)",
-                               "k_epilogue"};
+                               "k_epi_source", "k_epilogue (ports and transforms, side stream)"};
     if (!g) return "";
-    if (g->variant == 4) return (idx >= 0 && idx < 4) ? tb[idx] : "";
+    if (g->variant == 4) return (idx >= 0 && idx < 5) ? tb[idx] : "";
     if (g->variant == 3) return (idx >= 0 && idx < 2) ? skew[idx] : "";
     if (g->variant == 1) return (idx >= 0 && idx < 2) ? fused[idx] : "";
     if (g->variant == 2) return (idx >= 0 && idx < 2) ? tma[idx] : "";
@@ -1252,6 +1260,7 @@ yf_status yf_checkpoint_load(yf_grid *g, const char *path)
         if (b != g->cur)
             YF_CUDA_TRY(cudaMemcpy(g->buf[b], g->buf[g->cur], 6 * g->npts * g->esz, cudaMemcpyDeviceToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->ctr, &h.ctr, sizeof(long long), cudaMemcpyHostToDevice));
+    YF_CUDA_TRY(cudaMemcpy(g->ctr + 1, &h.ctr, sizeof(long long), cudaMemcpyHostToDevice));
     YF_CUDA_TRY(cudaMemcpy(g->status, &h.status, sizeof(int), cudaMemcpyHostToDevice));
     g->steps_done = h.steps;
     return YF_OK;

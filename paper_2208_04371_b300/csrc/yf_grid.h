@@ -115,6 +115,9 @@ void tb_free(yf_grid *g);
 cudaError_t tb_single(yf_grid *g, cudaStream_t s);
 cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev = nullptr);
 void tb_unchain(yf_grid *g);   // the next pair forks after everything queued before it
+// main stream waits for the port epilogues still running on the side stream (ends a run of
+// pairs; issued into the stream, so inside a capture too)
+cudaError_t tb_join(yf_grid *g, cudaStream_t s);
 int tb_launches_pair(const yf_grid *g);
 int tb_launches_single(const yf_grid *g);
 template <typename T>

@@ -129,8 +129,10 @@ struct EpiParams {
     float *acc32;    // [nf_total][4]
     float *kahan;    // [nf_total][8]  (sum, compensation) x 4
     double dy, dz;
-    long long *ctr;  // steps completed
-    int *status;     // bit 0: non-finite port sample
+    long long *ctr;      // steps whose ports and transforms are done
+    long long *src_ctr;  // steps whose source is added (equal to *ctr between calls)
+    int skip_source;     // 1: the source is added by k_epi_source on the critical path
+    int *status;         // bit 0: non-finite port sample
 };
 
 // kernel launchers (yf_kernels.cu)
@@ -140,6 +142,9 @@ template <typename T>
 cudaError_t launch_update_e(const StencilParams<T> &p, const Fields<T> &f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s);
+// the soft source alone (one block; step index and counter *p.src_ctr)
+template <typename T>
+cudaError_t launch_epi_source(const EpiParams<T> &p, cudaStream_t s);
 // one block per grid; eps holds two parameter sets (buffer parity 0, 1) per grid
 template <typename T>
 cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s);
@@ -212,6 +217,13 @@ struct TbPlan {
     // touches none of the nodes that epilogue reads or writes); valid while `chained`
     cudaEvent_t fork_next;
     bool chained;
+    // the port integrals and running transforms of each step run on pstream, off the
+    // critical path: ev_src (main stream, after a step's source) starts them; the next pair's
+    // box kernel waits for ev_p1 (after the first step's), and the frame step of the pair
+    // after it for ev_p2[parity] (after the second step's), before overwriting what they read
+    cudaStream_t pstream;
+    cudaEvent_t ev_src, ev_p1, ev_p2[2];
+    int npair;           // pairs issued since the last join
 };
 cudaError_t tb_prepare();
 cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,

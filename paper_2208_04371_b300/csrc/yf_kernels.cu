@@ -266,6 +266,7 @@ __device__ void epi_finish(const EpiParams<T> &P, long long n, const double (*vi
             if (!isfinite(vi[p][0]) || !isfinite(vi[p][1])) bad = 1;
         if (bad) atomicOr(P.status, 1);
         *P.ctr = n + 1;
+        if (!P.skip_source) *P.src_ctr = n + 1;
     }
 }
 
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
     const int tid = threadIdx.x;
     const long long n = *P.ctr;   // this is step n: E^{n+1}, H^{n+1/2} are in place
     for (int sg = blockIdx.x; sg < P.nseg; sg += gridDim.x) {
+        if (P.skip_source && P.segs[sg].kind == 0) continue;
         const double part = epi_segment(P, P.segs[sg], n, red);
         if (tid == 0 && P.segs[sg].kind != 0) P.slots[sg] = part;
     }
@@ -332,6 +334,34 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(EpiParams<T> P)
     }
     __syncthreads();
     epi_finish(P, n, vi);
+}
+
+// The soft source alone (Eq. 3), for the path that runs the port integrals and transforms on
+// a side stream: it is the only part of the epilogue that the next step reads.  One thread per
+// point of the source rectangle; each block evaluates the waveform once; its own step counter,
+// advanced by the last block to finish (ticket[1]), so that it may run ahead of the transforms.
+template <typename T>
+__global__ void __launch_bounds__(kEpiThreads) k_epi_source(EpiParams<T> P)
+{
+    __shared__ T add;
+    __shared__ bool last;
+    const long long n = *P.src_ctr;
+    if (threadIdx.x == 0)
+        add = (T)(P.amp * waveform(P.src_kind, P.p0, P.p1, P.t0, P.table, P.table_len, n + 1, P.dt));
+    __syncthreads();
+    const int nj = P.sj1 - P.sj0 + 1, npt = P.src_kind == YF_WAVE_NONE ? 0 : nj * (P.sk1 - P.sk0);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < npt; w += gridDim.x * blockDim.x) {
+        const int j = P.sj0 + w % nj, k = P.sk0 + w / nj;
+        const long q = (long)k * P.plane + (long)j * P.px + P.src_plane;
+        if (P.cls_z[q]) P.ez[q] += add;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(P.ticket + 1, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        P.ticket[1] = 0;
+        *P.src_ctr = n + 1;
+    }
 }
 
 // Many grids: block b runs the whole epilogue of grid b (parameters of the current parity).
@@ -425,6 +455,15 @@ __global__ void k_sanitize(Fields<T> F, const uint8_t *cx, const uint8_t *cy, co
 }  // namespace
 
 template <typename T>
+cudaError_t launch_epi_source(const EpiParams<T> &p, cudaStream_t s)
+{
+    const int npt = p.src_kind == YF_WAVE_NONE ? 0 : (p.sj1 - p.sj0 + 1) * (p.sk1 - p.sk0);
+    const int nblk = npt < kEpiThreads ? 1 : (npt + kEpiThreads - 1) / kEpiThreads;
+    k_epi_source<T><<<nblk < 296 ? nblk : 296, kEpiThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
@@ -486,6 +525,7 @@ cudaError_t launch_energy(const T *const c[6], const uint8_t *const cls[3], cons
     template cudaError_t launch_update_e<T>(const StencilParams<T> &, const Fields<T> &,     \
                                             cudaStream_t);                                  \
     template cudaError_t launch_epilogue<T>(const EpiParams<T> &, cudaStream_t);            \
+    template cudaError_t launch_epi_source<T>(const EpiParams<T> &, cudaStream_t);          \
     template cudaError_t launch_epilogue_batch<T>(const EpiParams<T> *, int, int, cudaStream_t); \
     template cudaError_t launch_sanitize<T>(const Fields<T> &, uint8_t *const[3], int, int, \
                                             int, int, long, cudaStream_t);                  \

@@ -103,10 +103,16 @@ void tb_free(yf_grid *g)
     cudaFree(t->items);
     cudaFree(t->args);
     cudaFree(t->maps);
+    if (t->pstream) cudaStreamSynchronize(t->pstream);
     if (t->fork) cudaEventDestroy(t->fork);
     if (t->fork_next) cudaEventDestroy(t->fork_next);
     if (t->join) cudaEventDestroy(t->join);
+    if (t->ev_src) cudaEventDestroy(t->ev_src);
+    if (t->ev_p1) cudaEventDestroy(t->ev_p1);
+    for (int q = 0; q < 2; ++q)
+        if (t->ev_p2[q]) cudaEventDestroy(t->ev_p2[q]);
     if (t->stream) cudaStreamDestroy(t->stream);
+    if (t->pstream) cudaStreamDestroy(t->pstream);
     delete t;
     g->tb = nullptr;
 }
@@ -225,9 +231,14 @@ yf_status tb_build(yf_grid *g)
         cudaMemcpy(t->maps, tm, sizeof(tm), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(YF_E_OOM, "variant 4: two-step arguments"));
     if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&t->pstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->fork_next, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_src, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_p1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_p2[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_p2[1], cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(YF_E_CUDA, "variant 4: stream set-up"));
     cudaError_t e = tb_prepare();
     if (e != cudaSuccess) return bail(cuda_fail(e, "variant 4: shared-memory opt-in"));
@@ -246,15 +257,42 @@ cudaError_t tb_single(yf_grid *g, cudaStream_t s)
     return cudaSuccess;
 }
 
+// A step's epilogue on the two-step path: the source (Eq. 3) on the main stream, where the
+// next step reads it; the port integrals (Eq. 4) and running transforms on the side stream,
+// after the source, recording `done` there.  ev (tracing, may be null) brackets the source on
+// s (q0, q0 + 1) and the side-stream kernel (q1, q1 + 1).
+static cudaError_t tb_epilogue(yf_grid *g, cudaStream_t s, cudaEvent_t done, const cudaEvent_t *ev, int q0,
+                               int q1)
+{
+    TbPlan &t = *g->tb;
+    cudaError_t e;
+    EpiParams<float> E = epi_params<float>(g);
+    if (ev && (e = cudaEventRecord(ev[q0], s)) != cudaSuccess) return e;
+    if ((e = launch_epi_source<float>(E, s)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[q0 + 1], s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t.ev_src, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(t.pstream, t.ev_src, 0)) != cudaSuccess) return e;
+    E.skip_source = 1;
+    if (ev && (e = cudaEventRecord(ev[q1], t.pstream)) != cudaSuccess) return e;
+    if ((e = launch_epilogue<float>(E, t.pstream)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[q1 + 1], t.pstream)) != cudaSuccess) return e;
+    return cudaEventRecord(done, t.pstream);
+}
+
 // two time steps with both epilogues: the box n -> n+2 on a side stream, concurrently the
 // frame n -> n+1 and its epilogue; then, once the box is done, the frame n+1 -> n+2 and its
-// epilogue
-// ev (tracing, may be null): 8 events recorded around the box kernel on its stream (0, 1) and
-// around each frame step and epilogue on s (2..4 first step, 5..7 second)
+// epilogue.  Buffers rotate A -> B -> C (B = A + 1, C = A + 2 mod 3), so the pair k+1 writes
+// the buffer that pair k's first port epilogue reads (its box kernel waits for ev_p1) and the
+// pair k+2 writes the one that pair k's second port epilogue reads (its first frame step waits
+// for ev_p2 of that parity); the first two pairs after a join need no such wait.
+// ev (tracing, may be null): 12 events: around the box kernel on its stream (0, 1), around
+// each frame step and source on s (2..4 first step, 5..7 second), around each side-stream port
+// epilogue (8, 9 and 10, 11)
 cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
 {
     TbPlan &t = *g->tb;
     const int r = g->cur, h = g->hpar, r1 = (r + 1) % 3;
+    const int k = t.npair;
     cudaError_t e;
     const bool box = t.count > 0;
     auto mark = [&](int q, cudaStream_t st) { return ev ? cudaEventRecord(ev[q], st) : cudaSuccess; };
@@ -264,6 +302,7 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
         // or port planes and writes neither of the buffers that epilogue uses
         if (!t.chained && (e = cudaEventRecord(t.fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(t.stream, t.chained ? t.fork_next : t.fork, 0)) != cudaSuccess) return e;
+        if (k >= 1 && (e = cudaStreamWaitEvent(t.stream, t.ev_p1, 0)) != cudaSuccess) return e;
         if ((e = mark(0, t.stream)) != cudaSuccess) return e;
         if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
         if ((e = mark(1, t.stream)) != cudaSuccess) return e;
@@ -271,14 +310,16 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
     } else if (ev) {
         if ((e = mark(0, s)) != cudaSuccess || (e = mark(1, s)) != cudaSuccess) return e;
     }
+    if (k >= 2 && (e = cudaStreamWaitEvent(s, t.ev_p2[k & 1], 0)) != cudaSuccess) return e;
     if ((e = mark(2, s)) != cudaSuccess) return e;
     if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r + h, g->status, s, &g->side)) != cudaSuccess) return e;
     g->cur = r1;
     g->hpar = h ^ 1;
     if ((e = mark(3, s)) != cudaSuccess) return e;
-    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
-    if ((e = mark(4, s)) != cudaSuccess) return e;
+    if ((e = tb_epilogue(g, s, t.ev_p1, ev, 3, 8)) != cudaSuccess) return e;
     if (box && (e = cudaStreamWaitEvent(s, t.join, 0)) != cudaSuccess) return e;
+    // the second frame step writes the buffer the previous pair's first port epilogue read
+    if (!box && k >= 1 && (e = cudaStreamWaitEvent(s, t.ev_p1, 0)) != cudaSuccess) return e;
     if ((e = mark(5, s)) != cudaSuccess) return e;
     if ((e = launch_tma_plan<float>(t.frame, g->tile_y, 2 * r1 + (h ^ 1), g->status, s, &g->side)) != cudaSuccess)
         return e;
@@ -289,18 +330,31 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
         if ((e = cudaEventRecord(t.fork_next, s)) != cudaSuccess) return e;
         t.chained = true;
     }
-    if ((e = launch_epilogue<float>(epi_params<float>(g), s)) != cudaSuccess) return e;
-    return mark(7, s);
+    if ((e = tb_epilogue(g, s, t.ev_p2[k & 1], ev, 6, 10)) != cudaSuccess) return e;
+    t.npair = k + 1;
+    return cudaSuccess;
+}
+
+cudaError_t tb_join(yf_grid *g, cudaStream_t s)
+{
+    TbPlan *t = g->tb;
+    if (!t || t->npair == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamWaitEvent(s, t->ev_p2[(t->npair - 1) & 1], 0);
+    t->npair = 0;
+    return e;
 }
 
 void tb_unchain(yf_grid *g)
 {
-    if (g->tb) g->tb->chained = false;
+    if (g->tb) {
+        g->tb->chained = false;
+        g->tb->npair = 0;
+    }
 }
 
 int tb_launches_pair(const yf_grid *g)
 {
-    return 2 * kinds_used(g->tb->frame) + (g->tb->count > 0) + 2;
+    return 2 * kinds_used(g->tb->frame) + (g->tb->count > 0) + 4;
 }
 
 int tb_launches_single(const yf_grid *g) { return kinds_used(g->tb->full) + 1; }

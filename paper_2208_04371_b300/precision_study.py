@@ -14,6 +14,10 @@ each accumulator set the study reports:
     S-matrix from the uniform-line extraction (Eq. 1-2, 5-6), which is FP64 in every case.
 
     python -m paper_2208_04371_b300.precision_study --steps 1000000 --out study.json
+
+With --lossy-line it instead runs the 768x384x256 lossy line on the benchmark's FP32 path
+(two steps per pass over the inner box) beside an FP64-field run of the same line and
+reports the field and S-parameter errors at the step counts of --marks.
 """
 from __future__ import annotations
 
@@ -101,6 +105,69 @@ def run(nsteps: int, ringing: bool, chunk: int = 50_000, checkpoints=(), log=pri
     return res
 
 
+def field_errors(g32: "yf.Grid", g64: "yf.Grid") -> dict:
+    """Relative L2 over all six components of the FP32 grid's fields against the FP64
+    grid's, ||F32 - F64|| / ||F64||, and the largest pointwise error relative to the largest
+    FP64 value; both grids' components are read into device buffers one at a time."""
+    import torch
+    p = g32.prob
+    shape = (p.nz + 1, p.ny + 1, p.nx + 1)
+    b32 = torch.empty(shape, dtype=torch.float32, device="cuda")
+    b64 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    err2 = ref2 = 0.0
+    emax = rmax = 0.0
+    for c in range(6):
+        yf.read_fields(g32.h, c, b32)
+        yf.read_fields(g64.h, c, b64)
+        d = b32.double() - b64
+        err2 += float(torch.sum(d * d))
+        ref2 += float(torch.sum(b64 * b64))
+        emax = max(emax, float(torch.max(torch.abs(d))))
+        rmax = max(rmax, float(torch.max(torch.abs(b64))))
+    return {"field_rel_l2": (err2 / ref2) ** 0.5 if ref2 > 0 else None,
+            "field_max_rel": emax / rmax if rmax > 0 else None}
+
+
+def lossy_line(marks=(2000, 20000), box_seg: int = 128, log=print) -> dict:
+    """The single large lossy line (768 x 384 x 256 cells of 20 nm) on the benchmark's path,
+    FP32 fields two steps per pass over the inner box, against the same line with FP64 fields
+    (FP64 accumulators both), advanced side by side.  At each step count: relative field L2
+    and pointwise error, and the S-parameter errors of the uniform-line extraction (S* and the
+    50-ohm S, complex difference and difference of magnitudes)."""
+    prob = W.config_lossy_line(nsteps=max(marks))
+    res = {"workload": prob.name, "cells": prob.cells, "fp32_path": "two steps per pass over "
+           f"the inner box (variant 4, kseg 32, box segments of {box_seg} planes)",
+           "fp64_path": "FP64 fields, one step per pass", "at": []}
+    t32 = t64 = 0.0
+    with yf.Grid(prob, prec=yf.FP32, variant=4, kseg=32, box_seg=box_seg) as g32, \
+            yf.Grid(prob, prec=yf.FP64) as g64:
+        if g32.dt != g64.dt:
+            raise RuntimeError("the two grids must share one time step")
+        done = 0
+        for m in sorted(marks):
+            n = m - done
+            t = time.perf_counter()
+            g32.step(n)
+            g32.sync()
+            t32 += time.perf_counter() - t
+            t = time.perf_counter()
+            g64.step(n)
+            g64.sync()
+            t64 += time.perf_counter() - t
+            done = m
+            s32, s64 = g32.sparams(), g64.sparams()
+            row = {"steps": m, **field_errors(g32, g64)}
+            for key in ("S_star", "S"):
+                row[f"{key}_abs_err"] = float(np.max(np.abs(s32[key] - s64[key])))
+                row[f"{key}_mag_err"] = float(np.max(np.abs(np.abs(s32[key]) - np.abs(s64[key]))))
+            row["max_abs_S21_fp64"] = float(np.max(np.abs(s64["S"][:, 1, 0])))
+            res["at"].append(row)
+            log(json.dumps({"workload": prob.name, **row}))
+    res["fp32_fields_gcell_s"] = prob.cells * done / t32 / 1e9
+    res["fp64_fields_gcell_s"] = prob.cells * done / t64 / 1e9
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=1_000_000)
@@ -108,7 +175,17 @@ def main():
     ap.add_argument("--accumulators-only", action="store_true",
                     help="skip the FP64-field reference grid (accumulator comparisons only)")
     ap.add_argument("--ringing-only", action="store_true")
+    ap.add_argument("--lossy-line", action="store_true",
+                    help="the 768x384x256 lossy line: FP32 fields on the benchmark's path against "
+                         "FP64 fields, at the step counts of --marks")
+    ap.add_argument("--marks", default="2000,20000")
     args = ap.parse_args()
+    if args.lossy_line:
+        result = lossy_line(tuple(int(x) for x in args.marks.split(",")))
+        with open(args.out, "w") as f:
+            json.dump(result, f, indent=1)
+        print(json.dumps(result))
+        return
     cps = [args.steps // 1000, args.steps // 100, args.steps // 10]
     variants = (True,) if args.ringing_only else (False, True)
     result = [run(args.steps, ringing, checkpoints=cps, with_fp64=not args.accumulators_only)

@@ -541,6 +541,9 @@ class Batch:
     def __init__(self, probs, prec=FP32, stream=None, dt: float = 0.0, tile_y: int = 8,
                  kseg: int = 16):
         self.probs = list(probs)
+        if dt <= 0.0:
+            # the instances' own Courant numbers: the smallest of their time steps
+            dt = min(courant_dt(p.dx, p.dy, p.dz, p.courant) for p in self.probs)
         n = len(self.probs)
         descs = (InstanceDesc * n)()
         self._keep = []

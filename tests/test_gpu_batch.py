@@ -93,3 +93,19 @@ def test_autotune_resets_state_and_caches(gpu, tmp_path):
         assert gt in (4, 8, 16) and gk in (8, 16, 32)
         assert gpu.steps_done(g.h) == 0 and not np.any(g.fields())
     assert len(json.load(open(cache))) == 2
+
+
+def test_batch_takes_the_instances_courant_number(gpu):
+    """A batch of lines built for CFL 0.9 (the on-chip line of Sec. III) steps with their own
+    time step, not with the library's default of 0.99 of the Courant limit: the batch's dt and
+    spectra equal the single-grid solver's bit for bit."""
+    p = W.config_cmos_line(nx=96, ny=40, nz=64, pml=6, nsteps=300, nfreq=8)
+    with gpu.Batch([p], prec=gpu.FP32) as b, gpu.Grid(p, prec=gpu.FP32) as g:
+        assert b.dt == g.dt
+        b.step(300)
+        g.step(300)
+        b.sync()
+        g.sync()
+        Vb, Ib = b.port_dfts(0)
+        Vg, Ig = g.port_dfts()
+    assert np.array_equal(Vb, Vg) and np.array_equal(Ib, Ig)

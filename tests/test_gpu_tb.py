@@ -164,8 +164,8 @@ def test_launch_count(gpu):
         pair = gpu.launches(g.h, 2)
         single = gpu.launches(g.h, 1)
         assert gpu.launches(g.h, 77) == 38 * pair + single
-        # frame kinds twice, the box kernel, two epilogues
-        assert 5 <= pair <= 13 and 2 <= single <= 6
+        # frame kinds twice, the box kernel, per step the source and the side-stream epilogue
+        assert 7 <= pair <= 15 and 2 <= single <= 6
 
 
 def test_checkpoint_resume_is_bitwise(gpu):
