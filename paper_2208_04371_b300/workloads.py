@@ -265,7 +265,8 @@ SIGMA_PD, SIGMA_AL = 9.5e6, 3.77e7
 
 def config_cmos_line(nx: int = 120, ny: int = 200, nz: int = 800, nsteps: int = 1_400_000,
                      driven: int = 0, uniform: bool = False, nfreq: int = 64, pml: int = 10,
-                     f_lo: float = 2e12, f_hi: float = 90e12) -> Problem:
+                     f_lo: float = 2e12, f_hi: float = 90e12, refine: int = 1,
+                     sigma: float = 10.146e-15) -> Problem:
     """The paper's third example (Sec. III), an on-chip line, in this build's frame
     (propagation along x): cells of 50 x 20 x 5 nm (the paper's 20 x 50 x 5 nm with x and y
     exchanged), 120 x 200 x 800 cells = 6 x 4 x 4 um; SiO2 (eps_r 3.9) everywhere else; CFL 0.9
@@ -282,43 +283,52 @@ def config_cmos_line(nx: int = 120, ny: int = 200, nz: int = 800, nsteps: int = 
     Ports: 1 at x = pml + 6 (V from the ground to the strip), 2 at x = nx - pml - 6 (V across
     the oxide gap from the Al to the strip); the source sits on the driven side, 4 cells
     outside its port.  uniform=True gives the incident-run line of Sec. II-A: the driven
-    port's cross-section along the whole length."""
-    dx, dy, dz = 50e-9, 20e-9, 5e-9
+    port's cross-section along the whole length.
+    refine = r divides every cell size by r and multiplies every cell count (grid, PML,
+    strip, step, port and source offsets) by r: the same line on a grid r times finer in
+    each direction (the Appendix's convergence test doubles it).  sigma is the width of the
+    Eq. 3 pulse (the Appendix's narrow pulse has 1.45 fs)."""
+    r = refine
+    dx, dy, dz = 50e-9 / r, 20e-9 / r, 5e-9 / r
+    nx, ny, nz, pml = nx * r, ny * r, nz * r, pml * r
     w = ny // 2
     j0 = (ny - w) // 2
     j1 = j0 + w
-    ks = nz // 2 - 3            # strip bottom, first half
-    kstep = 4                   # step height = oxide gap
+    ks = nz // 2 - 3 * r        # strip bottom, first half
+    kstep = 4 * r               # step height = oxide gap
+    thick = 6 * r               # strip thickness
     half = nx // 2
     ids = np.zeros((nz, ny, nx), dtype=np.uint8)   # 0 SiO2, 1 Pd, 2 Al
     for x0, x1, low in ((0, half, False), (half, nx, True)):
         lowered = low if not uniform else (driven == 1)
         kb = ks + (kstep if lowered else 0)
-        ids[kb:kb + 6, j0:j1, x0:x1] = 1
+        ids[kb:kb + thick, j0:j1, x0:x1] = 1
         if lowered:
             ids[:ks, :, x0:x1] = 2
     eps = np.array([3.9, 1.0, 1.0])
     sig = np.array([0.0, SIGMA_PD, SIGMA_AL])
-    p1, p2 = pml + 6, nx - pml - 6
-    ports = [Port(plane=p1, direction=1, j0=j0, j1=j1, k0=0, k1=ks, kb=ks, kt=ks + 6, margin=1),
+    p1, p2 = pml + 6 * r, nx - pml - 6 * r
+    ports = [Port(plane=p1, direction=1, j0=j0, j1=j1, k0=0, k1=ks, kb=ks, kt=ks + thick, margin=1),
              Port(plane=p2, direction=-1, j0=j0, j1=j1, k0=ks, k1=ks + kstep, kb=ks + kstep,
-                  kt=ks + kstep + 6, margin=1)]
+                  kt=ks + kstep + thick, margin=1)]
     if uniform and driven == 0:   # the first half's cross-section at both ports
-        ports[1] = Port(plane=p2, direction=-1, j0=j0, j1=j1, k0=0, k1=ks, kb=ks, kt=ks + 6, margin=1)
+        ports[1] = Port(plane=p2, direction=-1, j0=j0, j1=j1, k0=0, k1=ks, kb=ks, kt=ks + thick,
+                        margin=1)
     if uniform and driven == 1:   # the second half's cross-section at both ports
         ports[0] = Port(plane=p1, direction=1, j0=j0, j1=j1, k0=ks, k1=ks + kstep, kb=ks + kstep,
-                        kt=ks + kstep + 6, margin=1)
+                        kt=ks + kstep + thick, margin=1)
     if driven == 0:
-        src = Source(kind=WAVE_DIFF_GAUSS, plane=p1 - 4, j0=j0, j1=j1, k0=0, k1=ks, amplitude=1.0,
-                     param0=10.146e-15)
+        src = Source(kind=WAVE_DIFF_GAUSS, plane=p1 - 4 * r, j0=j0, j1=j1, k0=0, k1=ks,
+                     amplitude=1.0, param0=sigma)
     else:
-        src = Source(kind=WAVE_DIFF_GAUSS, plane=p2 + 4, j0=j0, j1=j1, k0=ks, k1=ks + kstep, amplitude=1.0,
-                     param0=10.146e-15)
+        src = Source(kind=WAVE_DIFF_GAUSS, plane=p2 + 4 * r, j0=j0, j1=j1, k0=ks, k1=ks + kstep,
+                     amplitude=1.0, param0=sigma)
     return Problem(nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz, courant=0.9, ids=ids, eps_r=eps,
                    sigma=sig, mu_r=np.ones(3), is_pec=np.zeros(3, np.uint8),
                    bc=(BC_PML, BC_PML, BC_PML, BC_PML, BC_PEC, BC_PML), pml_cells=pml,
                    source=src, ports=ports, freqs=linear_freqs(f_lo, f_hi, nfreq), nsteps=nsteps,
-                   name=f"cmos line {nx}x{ny}x{nz} driven {driven + 1}{' uniform' if uniform else ''}")
+                   name=f"cmos line {nx}x{ny}x{nz} driven {driven + 1}{' uniform' if uniform else ''}"
+                        + (f" refined x{r}" if r > 1 else ""))
 
 
 SURROGATE_LO = (4.0, 0.0, 6.0, 2.0, 0.0, 32.0)
