@@ -375,7 +375,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     kseg = args.kseg or (32 if args.variant == 4 else 16)
     g = yf.Grid(p, prec=yf.FP32, stream=stream.cuda_stream, variant=args.variant, kseg=kseg,
-                box_seg=args.box_seg if args.variant == 4 else 0)
+                box_seg=args.box_seg if args.variant == 4 else 0,
+                box_ty=args.box_ty if args.variant == 4 else 0)
     chunk = args.chunk
     launches_per_bench_step = yf.launches(g.h, chunk)
     box = yf.tb_box(g.h) if args.variant == 4 else None
@@ -498,6 +499,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": p.name, "cells": p.cells, "steps_per_bench_step": chunk,
                        "variant": args.variant, "tile_y": 8, "kseg": kseg,
                        "box_seg": (args.box_seg or 2 * kseg) if args.variant == 4 else None,
+                       "box_tile_y": args.box_ty if args.variant == 4 else None,
                        "inner_box": box,
                        "l2": "inputs larger than L2 (1.8 GB of fields)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -522,8 +524,10 @@ def main():
                     help="stencil variant: 4 two-step inner box (default), 2 one step per pass")
     ap.add_argument("--kseg", type=int, default=0,
                     help="z-planes per one-step block (0: 32 for variant 4, 16 for variant 2)")
-    ap.add_argument("--box-seg", type=int, default=128,
-                    help="variant 4: z-planes per two-step block (0: twice kseg; 128 cuts the lossy line's box into two)")
+    ap.add_argument("--box-seg", type=int, default=240,
+                    help="variant 4: z-planes per two-step block (0: twice kseg; 240: the lossy line's box in one segment per tile column)")
+    ap.add_argument("--box-ty", type=int, default=8, choices=[8, 16],
+                    help="variant 4: y rows per two-step block (16: one block per SM)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -172,19 +172,22 @@ yf_status yf_set_dft_mode(yf_grid *g, int mask);
  *      rest of the grid one step at a time, with the port epilogue after each step.  Uses a
  *      third field buffer (6 (nz+1)(ny+1) px words more, px = nx+1 rounded up to 32, allocated here or at the first step and
  *      freed when another variant is set).  An odd remaining step runs as variant 2.  The
- *      two-step blocks take 2 kseg z-planes each unless yf_set_box_segment says otherwise.
+ *      two-step blocks take 2 kseg z-planes each unless yf_set_box_shape says otherwise.
  * tile_y in {4, 8, 16}, 1 <= kseg <= 64.  All variants compute the same update; results agree to
  * rounding.  Drops captured graphs; may be called between steps.  YF_E_INVALID for variant 4
  * on an FP64 grid or on one with 6 (nz+1)(ny+1) px >= 2^31 (32-bit offsets in its kernel). */
 yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg);
 
-/* Variant 4: z-planes per block of the two-step kernel (planes >= 1), or 0 for the default
- * 2 kseg.  A tuning choice only: every segmentation gives the same fields bit for bit (each
- * block recomputes its halo planes from step-n data).  Longer segments re-read fewer halo
- * planes; the count of blocks decides how they pack onto the SMs and how much of the frame's
- * first step runs beside them.  Drops captured graphs; may be called between steps.
- * YF_E_INVALID for planes < 0. */
-yf_status yf_set_box_segment(yf_grid *g, int planes);
+/* Variant 4: the shape of the two-step kernel's blocks.  tile_y = 8 (0 selects it) or 16 nodes
+ * of y per block (32 of x either way; 8: two blocks per SM, 16: one block per SM, which
+ * recomputes fewer halo nodes); planes >= 1 z-planes per block, or 0 for the default 2 kseg.
+ * A tuning choice only: every shape gives the same fields bit for bit (each block
+ * recomputes its halo from step-n data).  Longer segments re-read fewer halo planes; the
+ * count of blocks decides how they pack onto the SMs and how much of the frame's first step
+ * runs beside them.  The inner box's y range is aligned to the larger of tile_y and the
+ * frame's tile height.  Drops captured graphs; may be called between steps.  YF_E_INVALID for
+ * another tile_y or planes < 0. */
+yf_status yf_set_box_shape(yf_grid *g, int tile_y, int planes);
 
 /* Variant 4's inner box as node ranges x0, x1, y0, y1, z0, z1 (inclusive; all -1 when the
  * grid has no box, which then steps one step at a time).  Finalises the geometry like a first

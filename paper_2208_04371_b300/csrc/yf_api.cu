@@ -1163,15 +1163,18 @@ yf_status yf_set_variant(yf_grid *g, int variant, int tile_y, int kseg)
     return YF_OK;
 }
 
-yf_status yf_set_box_segment(yf_grid *g, int planes)
+yf_status yf_set_box_shape(yf_grid *g, int tile_y, int planes)
 {
-    if (!g) return fail(YF_E_INVALID, "yf_set_box_segment: NULL grid");
-    if (planes < 0) return fail(YF_E_INVALID, "yf_set_box_segment: planes must be >= 0");
+    if (!g) return fail(YF_E_INVALID, "yf_set_box_shape: NULL grid");
+    if (tile_y != 0 && tile_y != 8 && tile_y != 16)
+        return fail(YF_E_INVALID, "yf_set_box_shape: tile_y must be 0, 8 or 16");
+    if (planes < 0) return fail(YF_E_INVALID, "yf_set_box_shape: planes must be >= 0");
     YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
     for (int b = 0; b < 6; ++b)
         if (g->graph[b]) { cudaGraphExecDestroy(g->graph[b]); g->graph[b] = nullptr; }
     const bool had_tb = g->tb != nullptr;
     if (had_tb) tb_free(g);
+    g->box_ty = tile_y == 0 ? 8 : tile_y;
     g->box_seg = planes;
     if (had_tb) return tb_build(g);
     return YF_OK;

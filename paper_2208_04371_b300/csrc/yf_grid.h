@@ -87,6 +87,7 @@ struct yf_grid {
     int tile_y = 8;               // fused: block rows (block is 32 x tile_y)
     int kseg = 16;                // fused: z-planes per block
     int box_seg = 0;              // variant 4: z-planes per two-step block (0: 2 kseg)
+    int box_ty = 8;               // variant 4: tile height of the two-step blocks (8 or 16)
     int chunk = 32;               // steps per captured graph (even)
     cudaGraphExec_t graph[6] = {};   // one per starting state cur * 2 + hpar
     yf::TbPlan *tb = nullptr;        // variant 4

@@ -190,10 +190,11 @@ void tma_items(int inst, int nx, int ny, int nz, int kseg, int tile_y, int n, co
 // the tensor maps), C receives E^{n+2}, H^{n+3/2} on the box, B the box's outer node layer at
 // E^{n+1}, H^{n+1/2}.  The box [bx0, bx1] x [by0, by1] x [bz0, bz1] is a union of 32 x 8 tiles.
 // tile and TMA boxes of the two-step kernel
-constexpr int kTbTileX = 32, kTbTileY = 8;   // output tile
-constexpr int kTbWinX = 40, kTbWinY = 12;    // E windows: x from i0-4, y from j0-2
-constexpr int kTbWinHY = 11;                 // H windows: the same x and first row, 11 rows
-constexpr int kTbClsX = 80, kTbClsY = 10;    // class tiles: x from i0-16, y from j0-1
+// output tile 32 x ty (ty = 8 or 16); E windows 40 x (ty + 4) nodes from (i0-4, j0-2), H windows
+// 40 x (ty + 3) from the same corner, class tiles 80 x (ty + 2) bytes from (i0-16, j0-1)
+constexpr int kTbTileX = 32;
+constexpr int kTbWinX = 40;
+constexpr int kTbClsX = 80;
 struct TbArgs {
     int px;
     long plane, npts;
@@ -211,6 +212,7 @@ struct TbPlan {
     TbArgs *args;        // [3] by source buffer
     CUtensorMap *maps;   // [3][window map, class map]
     int box[6];          // bx0, bx1, by0, by1, bz0, bz1
+    int ty;              // tile height of the two-step blocks (8 or 16)
     cudaStream_t stream;
     cudaEvent_t fork, join;
     // recorded by a pair before its last epilogue: the next pair's box kernel waits on it (it
@@ -227,7 +229,7 @@ struct TbPlan {
 };
 cudaError_t tb_prepare();
 cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,
-                       int phase, int *status, cudaStream_t s);
+                       int phase, int *status, cudaStream_t s, int tile_y);
 // skewed TMA-staged fused step (yf_skew.cu), same tensor maps as launch_tma
 cudaError_t skew_prepare();
 template <typename T>

@@ -1,6 +1,6 @@
 // Two-step (temporally blocked) Yee update of the inner box, FP32 (variant 4).
 //
-// The inner box is a set of whole 32 x 8 tiles and a z range that keep at least three nodes
+// The inner box is a set of whole 32 x TY tiles (TY = 8 or 16) and a z range that keep at least three nodes
 // from every CPML slab and domain wall and four from the source and port planes, so only the
 // plain Yee update (materials through the class table) happens in and around it.  One block
 // takes one tile over a z segment [kb, ke] and advances it from step n (buffer A) to step
@@ -22,12 +22,15 @@
 // between its two stages in registers.
 //
 // Step-n planes arrive by TMA two planes ahead, issued by an idle thread right after the
-// barrier: the E window of 40 x 12 nodes and the H window of 40 x 11 (x from i0-4, y from
-// j0-2) in four stages, and with plane p's fields the class tiles (80 x 10 bytes) of plane
-// p-1, in six slots (S4 reads the classes of plane q-4).  Every thread waits on a stage's
-// mbarrier itself.  H^{n+1/2} and E^{n+1} are kept for four planes and H^{n+3/2} for two, in
-// rings of rows of 44 floats (a 12-bank shift per row spreads the strips of eight rows over
-// all 32 banks) that hold only the rows each stage writes: 11, 10 and 9.
+// barrier: the E window of 40 x (TY + 4) nodes and the H window of 40 x (TY + 3) (x from
+// i0-4, y from j0-2) in four stages, and with plane p's fields the class tiles (80 x (TY + 2)
+// bytes) of plane p-1, in six slots (S4 reads the classes of plane q-4).  Every thread waits
+// on a stage's mbarrier itself.  H^{n+1/2} and E^{n+1} are kept for four planes and H^{n+3/2}
+// for two, in rings of rows of 44 floats (a 12-bank shift per row spreads the strips of eight
+// rows over all 32 banks) that hold only the rows each stage writes: TY + 3, TY + 2 and
+// TY + 1.  TY = 8 takes 113 KB of shared memory (two blocks of 384 threads per SM), TY = 16
+// 195 KB (one block of 672 threads), which recomputes 1.18 instead of 1.29 nodes per output
+// node.
 //
 // The single-step frame advances the rest of the grid n -> n+1 (A -> B) and n+1 -> n+2
 // (B -> C).  Its second step reads the box's outermost node layer at n + 1 from B (a window
@@ -46,32 +49,45 @@
 namespace yf {
 namespace {
 
-constexpr int TBX = kTbTileX, TBY = kTbTileY;         // output tile
-constexpr int NWARP = 12, TBN = 32 * NWARP;          // block
-constexpr int ISSUER = 223;                          // an idle thread of group A's last warp
-// windows: x from i0-4, y from j0-2; E with 12 rows, H with 11
-constexpr int WXN = kTbWinX, WN = WXN * kTbWinY, WNH = WXN * kTbWinHY;
-// rings, rows of 44 floats: H^{n+1/2} rows j0-2..j0+8, E^{n+1} and H^{n+3/2} from row j0-1
-constexpr int WXR = 44;
-constexpr int RHA = WXR * 11, REA = WXR * 10, RHB = WXR * 9;   // one component of a ring plane
-constexpr int CXN = kTbClsX, CYN = kTbClsY, CN = CXN * CYN;   // class tile: x from i0-16, y from j0-1
-constexpr int CSLOT = (3 * CN + 127) / 128 * 128;    // one class slot (bytes)
+constexpr int TBX = kTbTileX;                        // output tile width
+// windows: x from i0-4, 40 wide; rings: rows of 44 floats (a 12-bank shift per row spreads
+// the strips of eight rows over all 32 banks); class tiles: x from i0-16, 80 bytes wide
+constexpr int WXN = kTbWinX, WXR = 44, CXN = kTbClsX;
 constexpr int FST = 4, CSL = 6;                      // field stages, class slots
-constexpr int PLE = 3 * WN * 4;                      // E window of a stage (bytes)
-constexpr int PLH = (3 * WNH * 4 + 127) / 128 * 128; // H window of a stage (bytes)
-constexpr int SST = PLE + PLH;                       // one stage
-constexpr int C_OFF = FST * SST;
-constexpr int HA_OFF = C_OFF + CSL * CSLOT;          // H^{n+1/2} [4][3][RHA]
-constexpr int EA_OFF = HA_OFF + 4 * 3 * RHA * 4;     // E^{n+1}   [4][3][REA]
-constexpr int HB_OFF = EA_OFF + 4 * 3 * REA * 4;     // H^{n+3/2} [2][3][RHB]
-constexpr int CT_OFF = HB_OFF + 2 * 3 * RHB * 4;     // (Ca, Cb) per class
-constexpr int BAR_OFF = CT_OFF + 2 * kMaxClasses * 4;
-constexpr int TB_BYTES = BAR_OFF + 8 * FST;
-constexpr uint32_t TX_BYTES = 3 * WN * 4 + 3 * WNH * 4 + 3 * CN;
-static_assert(PLE % 128 == 0 && SST % 128 == 0 && C_OFF % 128 == 0 && CSLOT % 128 == 0,
-              "TMA destinations 128-byte aligned");
-static_assert(HA_OFF % 16 == 0 && EA_OFF % 16 == 0 && HB_OFF % 16 == 0, "ring planes 16-byte aligned");
-static_assert(2 * (TB_BYTES + 1024) <= 228 * 1024, "two blocks per SM");
+
+// Layout of a block whose output tile is 32 x TY nodes (TY = 8: two blocks per SM; TY = 16:
+// one).  Group A (S1, S2) works on rows j0-2..j0+TY, group B (S3, S4) on rows j0-1..j0+TY-1.
+template <int TY>
+struct TbShape {
+    static constexpr int RA = TY + 3, RB = TY + 1;                 // rows of groups A and B
+    static constexpr int NA = 18 * RA, NB = 17 * RB;               // their threads (pairs)
+    static constexpr int BBASE = (NA + 31) / 32 * 32;              // group B's first thread
+    static constexpr int TBN = BBASE + (NB + 31) / 32 * 32;        // block
+    static constexpr int ISSUER = BBASE - 1;                       // idle: BBASE > NA
+    static constexpr int WYN = TY + 4, WYH = TY + 3, CYN = TY + 2; // window / class-tile rows
+    static constexpr int WN = WXN * WYN, WNH = WXN * WYH, CN = CXN * CYN;
+    // rings: H^{n+1/2} rows j0-2..j0+TY, E^{n+1} rows j0-1..j0+TY, H^{n+3/2} j0-1..j0+TY-1
+    static constexpr int RHA = WXR * (TY + 3), REA = WXR * (TY + 2), RHB = WXR * (TY + 1);
+    static constexpr int CSLOT = (3 * CN + 127) / 128 * 128;       // one class slot (bytes)
+    static constexpr int PLE = 3 * WN * 4;                         // E window of a stage (bytes)
+    static constexpr int PLH = (3 * WNH * 4 + 127) / 128 * 128;    // H window of a stage (bytes)
+    static constexpr int SST = (PLE + 127) / 128 * 128 + PLH;      // one stage
+    static constexpr int PLE_PAD = SST - PLH;
+    static constexpr int C_OFF = FST * SST;
+    static constexpr int HA_OFF = C_OFF + CSL * CSLOT;             // H^{n+1/2} [4][3][RHA]
+    static constexpr int EA_OFF = HA_OFF + 4 * 3 * RHA * 4;        // E^{n+1}   [4][3][REA]
+    static constexpr int HB_OFF = EA_OFF + 4 * 3 * REA * 4;        // H^{n+3/2} [2][3][RHB]
+    static constexpr int CT_OFF = HB_OFF + 2 * 3 * RHB * 4;        // (Ca, Cb) per class
+    static constexpr int BAR_OFF = CT_OFF + 2 * kMaxClasses * 4;
+    static constexpr int BYTES = BAR_OFF + 8 * FST;
+    static constexpr uint32_t TX_BYTES = 3 * WN * 4 + 3 * WNH * 4 + 3 * CN;
+    static constexpr int BLOCKS_PER_SM = TY == 8 ? 2 : 1;
+    static_assert(NA < BBASE, "an idle thread issues the refills");
+    static_assert(SST % 128 == 0 && C_OFF % 128 == 0 && CSLOT % 128 == 0 && PLE_PAD % 128 == 0,
+                  "TMA destinations 128-byte aligned");
+    static_assert(HA_OFF % 16 == 0 && EA_OFF % 16 == 0 && HB_OFF % 16 == 0, "ring planes 16-byte aligned");
+    static_assert(BLOCKS_PER_SM * (BYTES + 1024) <= 228 * 1024, "shared memory per SM");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
@@ -115,10 +131,12 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
 // on the same pair of nodes.  A half-warp takes the first 16 pairs of one row (128 contiguous
 // bytes, no bank conflicts); the one or two pairs left at the right end of each row form
 // short strips:
-//   group A: threads   0..175 rows j0-2..j0+8, pairs 0..15 from i0-2;  176..197 pairs 16, 17
-//            (S1 on every row, S2 on rows j0-1..j0+8)
-//   group B: threads 224..367 rows j0-1..j0+7, pairs 0..15 from i0-2;  368..376 pair 16
-//            (S3 on every row, S4 on rows j0..j0+7 and pairs from i0)
+//   group A: rows j0-2..j0+TY: 16 (TY + 3) threads on pairs 0..15 from i0-2, then 2 (TY + 3)
+//            strip threads on pairs 16, 17 (S1 on every row, S2 on rows j0-1..j0+TY)
+//   group B: from the next warp, rows j0-1..j0+TY-1: 16 (TY + 1) threads on pairs 0..15
+//            from i0-2, then TY + 1 strip threads on pair 16 (S3 on every row, S4 on rows
+//            j0..j0+TY-1 and pairs from i0)
+// (TY = 8: group A threads 0..197, group B 224..376, 384 threads.)
 // Pairs reach one node past the needed ranges on the left of S2 and S3 and on the right of
 // S1 and S2; those extra nodes read neighbours nobody computed and feed nothing.  The pair's
 // values move as float2 (64-bit shared loads, one 32-bit load for the neighbour shifted by
@@ -143,16 +161,18 @@ __device__ __forceinline__ bool stage_pair(int e, int R, int extra, int *row, in
     return true;
 }
 
+template <int TY>
 __device__ __forceinline__ Task make_task(int tid, int i0, int j0, const TbArgs &P)
 {
+    using S = TbShape<TY>;
     Task k{0, 0, 0, 0, 0, 0, 0, false, false, false};
     int i = 0, j = 0, r, q;
-    if (tid < 224 && stage_pair(tid, 11, 2, &r, &q)) {
+    if (tid < S::BBASE && stage_pair(tid, S::RA, 2, &r, &q)) {
         k.kind = 1;
         k.e = r >= 1;
         i = i0 - 2 + 2 * q;
         j = j0 - 2 + r;
-    } else if (tid >= 224 && stage_pair(tid - 224, 9, 1, &r, &q)) {
+    } else if (tid >= S::BBASE && stage_pair(tid - S::BBASE, S::RB, 1, &r, &q)) {
         k.kind = 3;
         k.e = r >= 1 && q >= 1;
         i = i0 - 2 + 2 * q;
@@ -165,7 +185,7 @@ __device__ __forceinline__ Task make_task(int tid, int i0, int j0, const TbArgs 
     k.vb = k.ve;
     k.c = (j - j0 + 1) * CXN + (i - i0 + 16);
     k.g = j * P.px + i;
-    k.own = i >= i0 && i + 1 < i0 + TBX && j >= j0 && j < j0 + TBY;
+    k.own = i >= i0 && i + 1 < i0 + TBX && j >= j0 && j < j0 + TY;
     k.lay = i == P.bx0 || i + 1 == P.bx1 || j == P.by0 || j == P.by1;
     return k;
 }
@@ -224,8 +244,8 @@ __device__ __forceinline__ void h_pair(const float *e0, const float *e1, int w, 
 // thread's own H stage), ha = the ring of plane k (components HC apart, index v) for the y-
 // and x-neighbours, hpx/hpy = the pair's H_x, H_y on plane k-1 (the own H stage one plane
 // earlier), eo = the pair's E before the update, cl = class tile of plane k.  Class 0 (PEC)
-// has Ca = Cb = 0, so its edges stay zero.
-template <int HC>
+// has Ca = Cb = 0, so its edges stay zero; its three components are CN bytes apart.
+template <int HC, int CN>
 __device__ __forceinline__ void e_pair(const Vec3 &h, const float *ha, int v, float2 hpx, float2 hpy,
                                        const Vec3 &eo, const unsigned char *cl, const float2 *CT, int c,
                                        const Coef &K, float2 *vx, float2 *vy, float2 *vz)
@@ -249,17 +269,21 @@ __device__ __forceinline__ void e_pair(const Vec3 &h, const float *ha, int v, fl
                      __fmul2_rn(make_float2(az0.x, az1.x), eo.z));
 }
 
-__global__ void __launch_bounds__(TBN, 2)
+template <int TY>
+__global__ void __launch_bounds__(TbShape<TY>::TBN, TbShape<TY>::BLOCKS_PER_SM)
 k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, int phase_buf, int *status)
 {
+    using S = TbShape<TY>;
+    constexpr int TBN = S::TBN, ISSUER = S::ISSUER, SST = S::SST, CSLOT = S::CSLOT;
+    constexpr int WN = S::WN, WNH = S::WNH, RHA = S::RHA, REA = S::REA, RHB = S::RHB;
     extern __shared__ __align__(128) unsigned char sm[];
     const BatchItem it = items[blockIdx.x];
     const TbArgs P = args[phase_buf];
     const CUtensorMap *tmE = maps + 3 * phase_buf, *tmH = tmE + 1, *tmC = tmE + 2;
     const int tid = threadIdx.x;
     const int i0 = it.i0, j0 = it.j0, kb = it.kb, ke = it.ke;
-    float2 *CT = reinterpret_cast<float2 *>(sm + CT_OFF);
-    const uint32_t bar0 = smem_u32(sm + BAR_OFF);
+    float2 *CT = reinterpret_cast<float2 *>(sm + S::CT_OFF);
+    const uint32_t bar0 = smem_u32(sm + S::BAR_OFF);
     if (smem_u32(sm) & 127u) {
         if (tid == 0) atomicOr(status, 4);
         return;
@@ -276,10 +300,10 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     auto issue = [&](int p) {
         unsigned char *st = sm + (p & 3) * SST;
         const uint32_t bar = bar0 + 8 * (p & 3);
-        mbar_expect_tx(bar, TX_BYTES);
+        mbar_expect_tx(bar, S::TX_BYTES);
         tma_load_4d(smem_u32(st), tmE, i0 - 4, j0 - 2, p, 0, bar);
-        tma_load_4d(smem_u32(st + PLE), tmH, i0 - 4, j0 - 2, p, 3, bar);
-        tma_load_4d(smem_u32(sm + C_OFF + ((p + CSL - 1) % CSL) * CSLOT), tmC, i0 - 16, j0 - 1, p - 1, 0, bar);
+        tma_load_4d(smem_u32(st + S::PLE_PAD), tmH, i0 - 4, j0 - 2, p, 3, bar);
+        tma_load_4d(smem_u32(sm + S::C_OFF + ((p + CSL - 1) % CSL) * CSLOT), tmC, i0 - 16, j0 - 1, p - 1, 0, bar);
     };
     // every thread waits for each plane itself, once, in plane order; ph holds the parity of
     // each stage's next completion
@@ -296,7 +320,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         issue(kb - 1);
         issue(kb);
     }
-    const Task T = make_task(tid, i0, j0, P);
+    const Task T = make_task<TY>(tid, i0, j0, P);
     bool bad = !wait_plane(kb - 2);
 
     Coef K;
@@ -308,10 +332,10 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     K.nrz = make_float2(-P.rdz, -P.rdz);
     K.ndb = make_float2(-P.db, -P.db);
     const int plane = (int)P.plane, npts = (int)P.npts;
-    float *const HA = reinterpret_cast<float *>(sm + HA_OFF);
-    float *const EA = reinterpret_cast<float *>(sm + EA_OFF);
-    float *const HB = reinterpret_cast<float *>(sm + HB_OFF);
-    const bool xy_edge = i0 == P.bx0 || i0 + TBX - 1 == P.bx1 || j0 == P.by0 || j0 + TBY - 1 == P.by1;
+    float *const HA = reinterpret_cast<float *>(sm + S::HA_OFF);
+    float *const EA = reinterpret_cast<float *>(sm + S::EA_OFF);
+    float *const HB = reinterpret_cast<float *>(sm + S::HB_OFF);
+    const bool xy_edge = i0 == P.bx0 || i0 + TBX - 1 == P.bx1 || j0 == P.by0 || j0 + TY - 1 == P.by1;
     int b = (kb - 2) % CSL;   // class slot of plane q-1
     // carried z-neighbours: the E_x, E_y the H stage reads on the plane above (the next
     // plane's centre values), and the H_x, H_y the thread's H stage produced on the previous
@@ -328,15 +352,15 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         const unsigned char *s0 = sm + ((q - 1) & 3) * SST, *s1 = sm + (q & 3) * SST;
         const float *f0 = reinterpret_cast<const float *>(s0);          // step n: E, plane q-1
         const float *f1 = reinterpret_cast<const float *>(s1);          //         E, plane q
-        const float *g0 = reinterpret_cast<const float *>(s0 + PLE);    //         H, plane q-1
+        const float *g0 = reinterpret_cast<const float *>(s0 + S::PLE_PAD);   //   H, plane q-1
         float *haw = HA + ((q - 1) & 3) * 3 * RHA;           // H^{n+1/2} plane q-1
         const float *ha4 = HA + (q & 3) * 3 * RHA;           //           plane q-4
         float *eaw = EA + ((q - 1) & 3) * 3 * REA;           // E^{n+1}   plane q-1
         const float *ea4 = EA + (q & 3) * 3 * REA;           //           plane q-4
         const float *ea3 = EA + ((q + 1) & 3) * 3 * REA;     //           plane q-3
         float *hb4 = HB + (q & 1) * 3 * RHB;                 // H^{n+3/2} plane q-4
-        const unsigned char *cl1 = sm + C_OFF + b * CSLOT;                          // classes, plane q-1
-        const unsigned char *cl4 = sm + C_OFF + (b >= 3 ? b - 3 : b + 3) * CSLOT;   //          plane q-4
+        const unsigned char *cl1 = sm + S::C_OFF + b * CSLOT;                          // classes, plane q-1
+        const unsigned char *cl4 = sm + S::C_OFF + (b >= 3 ? b - 3 : b + 3) * CSLOT;   //          plane q-4
         const int p4 = q - 4;
 
         // phase 1: S1 on plane q-1 (group A), S3 on plane q-4 (group B)
@@ -365,7 +389,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         // pair is the thread's own H stage of the previous plane (c2x, c2y)
         if (T.kind == 1 && T.e && q >= kb && q <= ke + 2) {
             float2 vx, vy, vz;
-            e_pair<RHA>(hn, haw, T.vh, c2x, c2y, eo, cl1, CT, T.c, K, &vx, &vy, &vz);
+            e_pair<RHA, S::CN>(hn, haw, T.vh, c2x, c2y, eo, cl1, CT, T.c, K, &vx, &vy, &vz);
             st2(eaw + T.ve, vx);
             st2(eaw + REA + T.ve, vy);
             st2(eaw + 2 * REA + T.ve, vz);
@@ -384,7 +408,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
         }
         if (T.kind == 3 && T.e && q >= kb + 4) {
             float2 vx, vy, vz;
-            e_pair<RHB>(hn, hb4, T.vb, c2x, c2y, eo, cl4, CT, T.c, K, &vx, &vy, &vz);
+            e_pair<RHB, S::CN>(hn, hb4, T.vb, c2x, c2y, eo, cl4, CT, T.c, K, &vx, &vy, &vz);
             float *C = P.C + (p4 * plane + T.g);
             st2(C, vx);
             st2(C + npts, vy);
@@ -405,14 +429,20 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
 
 cudaError_t tb_prepare()
 {
-    return cudaFuncSetAttribute(k_yee_tb2, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_yee_tb2<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TbShape<8>::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_yee_tb2<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TbShape<16>::BYTES);
 }
 
 cudaError_t launch_tb2(const BatchItem *items, int count, const TbArgs *args, const CUtensorMap *maps,
-                       int phase, int *status, cudaStream_t s)
+                       int phase, int *status, cudaStream_t s, int tile_y)
 {
     if (count <= 0) return cudaSuccess;
-    k_yee_tb2<<<count, TBN, TB_BYTES, s>>>(items, args, maps, phase, status);
+    if (tile_y == 16)
+        k_yee_tb2<16><<<count, TbShape<16>::TBN, TbShape<16>::BYTES, s>>>(items, args, maps, phase, status);
+    else
+        k_yee_tb2<8><<<count, TbShape<8>::TBN, TbShape<8>::BYTES, s>>>(items, args, maps, phase, status);
     return cudaGetLastError();
 }
 

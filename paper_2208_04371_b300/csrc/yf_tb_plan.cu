@@ -55,7 +55,7 @@ bool choose_box(const yf_grid *g, int box[6])
         run = ok ? run + 1 : 0;
         if (run > best) { best = run; bt0 = tx - run + 1; }
     }
-    const int A = std::max(8, g->tile_y);
+    const int A = std::max(g->box_ty, g->tile_y);
     const int by0 = (YL + 3 + A - 1) / A * A, byE = (YH - 2) / A * A;
     const int bz0 = ZL + 3, bz1 = ZH - 3;
     if (best < 1 || byE <= by0 || bz1 - bz0 + 1 < 4) return false;
@@ -135,6 +135,7 @@ yf_status tb_build(yf_grid *g)
 
     std::vector<BatchItem> full[5], frame[5], two;
     tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full, 8);
+    t->ty = g->box_ty;
     const bool have_box = choose_box(g, t->box);
     const int *B = t->box;
     for (int k = 0; k < 5; ++k)
@@ -147,13 +148,13 @@ yf_status tb_build(yf_grid *g)
             if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
             if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
         }
-    // z-planes per two-step block: as set by yf_set_box_segment, else twice the one-step
+    // z-planes per two-step block: as set by yf_set_box_shape, else twice the one-step
     // segment (the two-step block re-reads four halo planes instead of two); its rings are
     // indexed modulo their depth, so any length works
     const int seg = g->box_seg > 0 ? g->box_seg : 2 * g->kseg;
     if (have_box)
         for (int kb = B[4]; kb <= B[5]; kb += seg)
-            for (int j0 = B[2]; j0 <= B[3]; j0 += kTbTileY)
+            for (int j0 = B[2]; j0 <= B[3]; j0 += t->ty)
                 for (int i0 = B[0]; i0 <= B[1]; i0 += kTbTileX)
                     two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + seg - 1)});
     yf_status st;
@@ -192,11 +193,11 @@ yf_status tb_build(yf_grid *g)
     CUtensorMap tm[9];
     const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
     const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
-    const cuuint32_t wbox[4] = {kTbWinX, kTbWinY, 1, 3};
-    const cuuint32_t hbox[4] = {kTbWinX, kTbWinHY, 1, 3};
+    const cuuint32_t wbox[4] = {kTbWinX, (cuuint32_t)t->ty + 4, 1, 3};
+    const cuuint32_t hbox[4] = {kTbWinX, (cuuint32_t)t->ty + 3, 1, 3};
     const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
     const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
-    const cuuint32_t cbox[4] = {kTbClsX, kTbClsY, 1, 3};
+    const cuuint32_t cbox[4] = {kTbClsX, (cuuint32_t)t->ty + 2, 1, 3};
     const cuuint32_t one[4] = {1, 1, 1, 1};
     for (int r = 0; r < 3; ++r) {
         TbArgs &a = ta[r];
@@ -304,7 +305,8 @@ cudaError_t tb_pair(yf_grid *g, cudaStream_t s, const cudaEvent_t *ev)
         if ((e = cudaStreamWaitEvent(t.stream, t.chained ? t.fork_next : t.fork, 0)) != cudaSuccess) return e;
         if (k >= 1 && (e = cudaStreamWaitEvent(t.stream, t.ev_p1, 0)) != cudaSuccess) return e;
         if ((e = mark(0, t.stream)) != cudaSuccess) return e;
-        if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream)) != cudaSuccess) return e;
+        if ((e = launch_tb2(t.items, t.count, t.args, t.maps, r, g->status, t.stream, t.ty)) != cudaSuccess)
+            return e;
         if ((e = mark(1, t.stream)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(t.join, t.stream)) != cudaSuccess) return e;
     } else if (ev) {

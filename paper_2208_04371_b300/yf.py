@@ -108,7 +108,7 @@ _SIGS = {
     "yf_sparams_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "yf_reset": (_i, [_vp]),
     "yf_set_variant": (_i, [_vp, _i, _i, _i]),
-    "yf_set_box_segment": (_i, [_vp, _i]),
+    "yf_set_box_shape": (_i, [_vp, _i, _i]),
     "yf_profile_steps": (_i, [_vp, C.c_long, _dp, C.POINTER(_i)]),
     "yf_kernel_name": (C.c_char_p, [_vp, _i]),
     "yf_autotune": (_i, [_vp, C.c_char_p, _i, C.POINTER(_i), C.POINTER(_i)]),
@@ -373,9 +373,10 @@ def set_variant(g, variant, tile_y=8, kseg=16):
     _check(_lib.yf_set_variant(C.c_void_p(g), variant, tile_y, kseg))
 
 
-def set_box_segment(g, planes):
-    """Variant 4: z-planes per two-step block (0: twice kseg); the fields do not depend on it."""
-    _check(_lib.yf_set_box_segment(C.c_void_p(g), int(planes)))
+def set_box_shape(g, tile_y=0, planes=0):
+    """Variant 4: tile height (8 or 16; 0: 8) and z-planes (0: twice kseg) of the two-step
+    blocks; the fields do not depend on either."""
+    _check(_lib.yf_set_box_shape(C.c_void_p(g), int(tile_y), int(planes)))
 
 
 def autotune(g, cache_path=None, reps=4):
@@ -438,7 +439,7 @@ class Grid:
     def __init__(self, prob, prec=FP32, stream=None, dt: Optional[float] = None,
                  dft_mask: int = DFT_FP64, with_source: bool = True, with_ports: bool = True,
                  variant: Optional[int] = None, tile_y: int = 8, kseg: int = 16,
-                 box_seg: int = 0):
+                 box_seg: int = 0, box_ty: int = 0):
         self.prob = prob
         self.prec = prec
         if dt is None:
@@ -465,8 +466,8 @@ class Grid:
             set_dft_mode(self.h, dft_mask)
             if variant is not None:
                 set_variant(self.h, variant, tile_y, kseg)
-            if box_seg:
-                set_box_segment(self.h, box_seg)
+            if box_seg or box_ty:
+                set_box_shape(self.h, box_ty, box_seg)
         except Exception:
             grid_destroy(self.h)
             self.h = None

@@ -30,8 +30,8 @@ def rel_l2(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
-def _tb_problem(port_mid=False):
-    nx, ny, nz = 170, 70, 50
+def _tb_problem(port_mid=False, ny=70):
+    nx, nz = 170, 50
     rng = W.SplitMix64(0x7B2)
     ids = np.array([rng.randint(0, 4) for _ in range(nx * ny * nz)], np.uint8).reshape(nz, ny, nx)
     ids[20:26, 30:38, 60:75] = 5
@@ -130,19 +130,22 @@ def test_graph_chunks_equal_direct_pairs(gpu):
         assert np.array_equal(a.port_dfts()[0], b.port_dfts()[0])
 
 
-@pytest.mark.parametrize("box_seg", [3, 14, 37])
-def test_box_segmentation_does_not_change_the_fields(gpu, box_seg):
+@pytest.mark.parametrize("box_ty,box_seg", [(8, 3), (8, 14), (8, 37), (16, 0), (16, 9)])
+def test_box_shape_does_not_change_the_fields(gpu, box_ty, box_seg):
     """The box's 37 planes cut into segments of 3 (the shortest the rings allow, thirteen
-    segments), 14 (a ragged last segment of 9) or 37 (one segment), against the default
-    (32 planes, then 5): each block recomputes its halo planes from step-n data, so the
-    fields and spectra agree bit for bit, also after the segmentation changes mid-run."""
-    p = _tb_problem()
+    segments), 14 (a ragged last segment of 9) or 37 (one segment), and blocks 16 rows high
+    (one block per SM), against the default (8 rows, 32 planes then 5), on the test grid made
+    78 nodes wide so that its box (y 16..63) holds whole tiles of either height: each block
+    recomputes its halo from step-n data, so the fields and spectra agree bit for bit, also
+    after the shape changes mid-run."""
+    p = _tb_problem(ny=78)
     with gpu.Grid(p, prec=gpu.FP32, variant=4) as a, \
-            gpu.Grid(p, prec=gpu.FP32, variant=4, box_seg=box_seg) as b:
+            gpu.Grid(p, prec=gpu.FP32, variant=4, box_seg=box_seg, box_ty=box_ty) as b:
+        assert gpu.tb_box(a.h) == gpu.tb_box(b.h) == (32, 127, 16, 63, 3, 39)
         a.step(40)
         b.step(40)
         assert np.array_equal(a.fields(), b.fields())
-        gpu.set_box_segment(b.h, 0)
+        gpu.set_box_shape(b.h, 0, 0)
         a.step(21)
         b.step(21)
         assert np.array_equal(a.fields(), b.fields())
@@ -150,12 +153,13 @@ def test_box_segmentation_does_not_change_the_fields(gpu, box_seg):
         assert np.array_equal(a.port_dfts()[1], b.port_dfts()[1])
 
 
-def test_box_segment_rejects_negative(gpu):
+def test_box_shape_rejects_bad_arguments(gpu):
     p = _tb_problem()
     with gpu.Grid(p, prec=gpu.FP32, variant=4) as g:
-        with pytest.raises(gpu.YFError) as e:
-            gpu.set_box_segment(g.h, -1)
-        assert e.value.code == gpu.E_INVALID
+        for ty, seg in ((12, 0), (8, -1)):
+            with pytest.raises(gpu.YFError) as e:
+                gpu.set_box_shape(g.h, ty, seg)
+            assert e.value.code == gpu.E_INVALID
 
 
 def test_launch_count(gpu):
