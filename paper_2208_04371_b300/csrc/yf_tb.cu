@@ -296,7 +296,8 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     __syncthreads();
 
     // one thread: step-n plane p -> field stage p & 3 (E and H windows), and the class tiles of
-    // plane p - 1 -> slot (p - 1) mod 6, all on the stage's mbarrier (kb >= 3, so p - 1 >= 0)
+    // plane p - 1 -> slot (p - 1) mod 6, all on the stage's mbarrier (p >= kb - 2 >= -2; planes
+    // below the grid, for a box on the ground, arrive as zeros)
     auto issue = [&](int p) {
         unsigned char *st = sm + (p & 3) * SST;
         const uint32_t bar = bar0 + 8 * (p & 3);
@@ -336,7 +337,7 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     float *const EA = reinterpret_cast<float *>(sm + S::EA_OFF);
     float *const HB = reinterpret_cast<float *>(sm + S::HB_OFF);
     const bool xy_edge = i0 == P.bx0 || i0 + TBX - 1 == P.bx1 || j0 == P.by0 || j0 + TY - 1 == P.by1;
-    int b = (kb - 2) % CSL;   // class slot of plane q-1
+    int b = (kb - 2 + CSL) % CSL;   // class slot of plane q-1 (kb >= 0)
     // carried z-neighbours: the E_x, E_y the H stage reads on the plane above (the next
     // plane's centre values), and the H_x, H_y the thread's H stage produced on the previous
     // plane (the E stage's lower z-neighbour)

@@ -33,7 +33,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
 // them (the values at i0+33 and i0+34 only feed nodes nobody uses); the nodes it needs must
 // see the plain update only.  So the box keeps three nodes from every
 // absorbing slab and domain wall on the low sides and two (x, y) or three (z) on the high
-// sides, and tiles whose x range widened by four nodes holds the source plane or a port plane
+// sides, except that it reaches down to a PEC wall at z = 0 (the ground): there the planes it
+// reads below the grid arrive as zeros, which is what the wall's edges hold, and its stores
+// stay in the grid.  Tiles whose x range widened by four nodes holds the source plane or a port plane
 // are left out (the port epilogue reads and the source writes the frame's fields between
 // the two steps).  x: the longest run of admissible 32-node tile columns; y: rows aligned to
 // the frame's tile height; z: every admissible plane.  Returns false when no box fits.
@@ -57,7 +59,7 @@ bool choose_box(const yf_grid *g, int box[6])
     }
     const int A = std::max(g->box_ty, g->tile_y);
     const int by0 = (YL + 3 + A - 1) / A * A, byE = (YH - 2) / A * A;
-    const int bz0 = ZL + 3, bz1 = ZH - 3;
+    const int bz0 = g->pml_lo[2] ? ZL + 3 : 0, bz1 = ZH - 3;
     if (best < 1 || byE <= by0 || bz1 - bz0 + 1 < 4) return false;
     box[0] = 32 * bt0;
     box[1] = 32 * (bt0 + best) - 1;

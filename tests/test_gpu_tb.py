@@ -1,10 +1,10 @@
 """Variant 4 (two time steps per pass over the inner box, FP32) through the C ABI.
 
 The grid is 170 x 70 x 50 nodes with random lossy materials, a PEC block and PEC sheets that
-cross the box boundary, CPML on five faces, a source plane and two port planes near the x
-ends.  Its box is x 32..127, y 16..55, z 3..39: three tile columns, five tile rows and two
-z segments of the two-step kernel (32 planes, then a ragged 5), surrounded by every kind of
-single-step frame work.  A second geometry moves a port plane to the middle, which splits the
+cross the box boundary, CPML on five faces (the ground at z = 0 is PEC), a source plane and
+two port planes near the x ends.  Its box is x 32..127, y 16..55, z 0..39: three tile columns,
+five tile rows and two z segments of the two-step kernel (32 planes from the ground, then a
+ragged 8), surrounded by every kind of single-step frame work.  A second geometry moves a port plane to the middle, which splits the
 admissible tile columns (the box takes the longest run of them).
 
 Bars (the FP32 budget used for every variant): fields relative L2 <= 1e-5 against the FP64
@@ -23,7 +23,7 @@ from paper_2208_04371_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-BOX = (32, 127, 16, 55, 3, 39)
+BOX = (32, 127, 16, 55, 0, 39)
 
 
 def rel_l2(a, b):
@@ -65,7 +65,7 @@ def test_box_is_the_documented_one(gpu):
         assert gpu.tb_box(g.h) == BOX
     with gpu.Grid(_tb_problem(port_mid=True), prec=gpu.FP32, variant=4) as g:
         # admissible tile columns: 1 (x 32..63), then 3 and 4 past the port at x = 90
-        assert gpu.tb_box(g.h) == (96, 159, 16, 55, 3, 39)
+        assert gpu.tb_box(g.h) == (96, 159, 16, 55, 0, 39)
 
 
 @pytest.mark.parametrize("tile_y,kseg", [(8, 16), (4, 5), (16, 7), (8, 1), (8, 32)])
@@ -132,16 +132,16 @@ def test_graph_chunks_equal_direct_pairs(gpu):
 
 @pytest.mark.parametrize("box_ty,box_seg", [(8, 3), (8, 14), (8, 37), (16, 0), (16, 9)])
 def test_box_shape_does_not_change_the_fields(gpu, box_ty, box_seg):
-    """The box's 37 planes cut into segments of 3 (the shortest the rings allow, thirteen
-    segments), 14 (a ragged last segment of 9) or 37 (one segment), and blocks 16 rows high
-    (one block per SM), against the default (8 rows, 32 planes then 5), on the test grid made
+    """The box's 40 planes cut into segments of 3 (fourteen segments, the last of one plane),
+    14 (a ragged last segment of 12) or 37 (then 3), and blocks 16 rows high (one block per
+    SM), against the default (8 rows, 32 planes then 8), on the test grid made
     78 nodes wide so that its box (y 16..63) holds whole tiles of either height: each block
     recomputes its halo from step-n data, so the fields and spectra agree bit for bit, also
     after the shape changes mid-run."""
     p = _tb_problem(ny=78)
     with gpu.Grid(p, prec=gpu.FP32, variant=4) as a, \
             gpu.Grid(p, prec=gpu.FP32, variant=4, box_seg=box_seg, box_ty=box_ty) as b:
-        assert gpu.tb_box(a.h) == gpu.tb_box(b.h) == (32, 127, 16, 63, 3, 39)
+        assert gpu.tb_box(a.h) == gpu.tb_box(b.h) == (32, 127, 16, 63, 0, 39)
         a.step(40)
         b.step(40)
         assert np.array_equal(a.fields(), b.fields())
@@ -206,7 +206,7 @@ def test_lossy_line_variant4_matches_variant2_at_full_size(gpu):
     for v in (2, 4):
         with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
             if v == 4:
-                assert gpu.tb_box(g.h) == (32, 735, 16, 367, 3, 241)
+                assert gpu.tb_box(g.h) == (32, 735, 16, 367, 0, 241)
             g.step(64)
             g.sync()
             out[v] = (g.fields(), *g.port_dfts())
@@ -239,7 +239,8 @@ def test_grid_without_a_box_steps_exactly_like_variant2(gpu):
 
 def test_pec_cavity_variant4_matches_variant2(gpu):
     """A closed lossless PEC cavity (no CPML, source or ports) from seeded random fields: the
-    box then reaches three nodes from every wall.  200 steps, two-step path against one-step."""
+    box then reaches three nodes from every wall but the one at z = 0, where it starts.  200
+    steps, two-step path against one-step."""
     nx, ny, nz = 100, 60, 40
     p = W.Problem(nx=nx, ny=ny, nz=nz, dx=1e-3, dy=0.8e-3, dz=1.1e-3, courant=0.95,
                   ids=np.zeros((nz, ny, nx), np.uint8), eps_r=np.array([1.0]),
@@ -251,7 +252,7 @@ def test_pec_cavity_variant4_matches_variant2(gpu):
     for v in (2, 4):
         with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
             if v == 4:
-                assert gpu.tb_box(g.h) == (32, 95, 8, 55, 3, 37)
+                assert gpu.tb_box(g.h) == (32, 95, 8, 55, 0, 37)
             g.set_fields(f0)
             g.step(200)
             g.sync()
@@ -287,7 +288,7 @@ def test_reset_and_new_materials_resolve_bitwise(gpu, variant):
 
 def test_single_tile_box_matches_variant2(gpu):
     """A 67 x 19 x 20 closed PEC cavity from seeded random fields: its box is one 32 x 8 tile
-    (x 32..63, y 8..15, z 3..17), so a single block writes the outer node layer on all four
+    (x 32..63, y 8..15, z 0..17), so a single block writes the outer node layer on all four
     sides and both z faces.  301 steps (150 pairs and one single step), two-step path against
     one-step within the FP32 budget."""
     nx, ny, nz = 67, 19, 20
@@ -301,7 +302,7 @@ def test_single_tile_box_matches_variant2(gpu):
     for v in (2, 4):
         with gpu.Grid(p, prec=gpu.FP32, variant=v) as g:
             if v == 4:
-                assert gpu.tb_box(g.h) == (32, 63, 8, 15, 3, 17)
+                assert gpu.tb_box(g.h) == (32, 63, 8, 15, 0, 17)
             g.set_fields(f0)
             g.step(301)
             g.sync()
