@@ -213,9 +213,10 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": p.name, "cells": p.cells,
                                         "steps_per_bench_step": nsteps,
-                                        "sample_spread": [min(rates), max(rates)]},
+                                        "l2": "inputs larger than L2 (host memory)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": desc + f"; median of {len(rates)} samples"},
+                         "sample": desc + f"; median of {len(rates)} samples (spread "
+                                          f"{min(rates):.3f}-{max(rates):.3f})"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
