@@ -320,14 +320,19 @@ def _subbox_check(f0, f1, prob, box, nsteps, dt, tol):
     assert err <= tol, err
 
 
-def test_full_size_lossy_line_sampled_parity(gpu):
-    """The 768x384x256 lossy line (FP32, the benchmark workload and launch configuration):
-    after 120 steps, 8 more GPU steps agree element-wise with the oracle run on a sub-box
-    seeded with the GPU state (strip, oxide layers and Si inside the box)."""
+@pytest.mark.parametrize("variant,kseg,box_seg", [(4, 32, 240), (2, 16, 0)])
+def test_full_size_lossy_line_sampled_parity(gpu, variant, kseg, box_seg):
+    """The 768x384x256 lossy line (FP32, the benchmark workload), in the benchmark's launch
+    configuration (two steps per pass over the inner box, one box segment per tile column) and
+    on the one-step path: after 120 steps, 8 more GPU steps agree element-wise with the oracle
+    run on a sub-box seeded with the GPU state.  The sub-box (x 22..70) straddles the CPML frame
+    and the inner box (from x = 32), around the strip, the oxide layers and the Si."""
     p = W.config_lossy_line(nsteps=0)
     j0, j1 = p.ports[0].j0, p.ports[0].j1
     box = ((22, 70), ((j0 + j1) // 2 - 30, (j0 + j1) // 2 + 30), (170, 226))
-    with gpu.Grid(p, prec=gpu.FP32) as g:
+    with gpu.Grid(p, prec=gpu.FP32, variant=variant, kseg=kseg, box_seg=box_seg) as g:
+        if variant == 4:
+            assert gpu.tb_box(g.h) == (32, 735, 16, 367, 0, 241)
         g.step(120)
         f0 = g.fields(box)
         g.step(8)
@@ -361,3 +366,25 @@ def test_rlcg_kernel_matches_oracle_on_synthetic_lines(gpu):
         assert np.all(np.abs(got["R"][ok] - ref["R"][ok]) <= tol * w[ok] * L)
         assert np.all(np.abs(got["G"][ok] - ref["G"][ok]) <= tol * w[ok] * C)
         assert np.all(np.abs(got["gamma"][ok] - ref["gamma"][ok]) <= tol * np.abs(ref["gamma"][ok]))
+
+
+def test_full_size_lossy_line_whole_grid_parity_in_the_benchmark_configuration(gpu):
+    """The benchmark itself, checked everywhere: the 768x384x256 lossy line for 128 steps (two
+    graph chunks of the benchmark's 64) on its path (two steps per pass over the inner box,
+    kseg 32, one box segment per tile column, the port epilogue on a side stream) against the
+    FP64 oracle over the whole grid (16 GB of host memory, about half a minute on the host's
+    cores): all six fields within the FP32 budget of 1e-5 relative L2, and the port spectra
+    within 1e-4 of their maximum."""
+    p = W.config_lossy_line(nsteps=128)
+    ref = yee.run(p, want_fields=True)
+    with gpu.Grid(p, prec=gpu.FP32, variant=4, kseg=32, box_seg=240) as g:
+        assert gpu.tb_box(g.h) == (32, 735, 16, 367, 0, 241)
+        g.step(64)
+        g.step(64)
+        g.sync()
+        f = g.fields()
+        V, I = g.port_dfts()
+    assert rel_l2(f, ref["fields"]) <= 1e-5
+    Vo, Io = post.port_dfts(ref["V"], ref["I"], p.freqs, ref["dt"])
+    assert np.max(np.abs(V - Vo)) <= 1e-4 * np.max(np.abs(Vo))
+    assert np.max(np.abs(I - Io)) <= 1e-4 * np.max(np.abs(Io))
