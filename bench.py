@@ -525,8 +525,8 @@ def main():
                     help="stencil variant: 4 two-step inner box (default), 2 one step per pass")
     ap.add_argument("--kseg", type=int, default=0,
                     help="z-planes per one-step block (0: 32 for variant 4, 16 for variant 2)")
-    ap.add_argument("--box-seg", type=int, default=240,
-                    help="variant 4: z-planes per two-step block (0: twice kseg; 240: the lossy line's box in one segment per tile column)")
+    ap.add_argument("--box-seg", type=int, default=-1,
+                    help="variant 4: z-planes per two-step block (0: twice kseg; default nz: the box in one segment per tile column)")
     ap.add_argument("--box-ty", type=int, default=8, choices=[8, 16],
                     help="variant 4: y rows per two-step block (16: one block per SM)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -546,6 +546,8 @@ def main():
     ap.add_argument("--clocks-dir", default="",
                     help="directory for the raw nvidia-smi clock samples (default: the system temp directory)")
     args = ap.parse_args()
+    if args.box_seg < 0:
+        args.box_seg = args.nz   # at least the box's depth: one segment per tile column
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -320,7 +320,7 @@ def _subbox_check(f0, f1, prob, box, nsteps, dt, tol):
     assert err <= tol, err
 
 
-@pytest.mark.parametrize("variant,kseg,box_seg", [(4, 32, 240), (2, 16, 0)])
+@pytest.mark.parametrize("variant,kseg,box_seg", [(4, 32, 256), (2, 16, 0)])
 def test_full_size_lossy_line_sampled_parity(gpu, variant, kseg, box_seg):
     """The 768x384x256 lossy line (FP32, the benchmark workload), in the benchmark's launch
     configuration (two steps per pass over the inner box, one box segment per tile column) and
@@ -377,7 +377,7 @@ def test_full_size_lossy_line_whole_grid_parity_in_the_benchmark_configuration(g
     within 1e-4 of their maximum."""
     p = W.config_lossy_line(nsteps=128)
     ref = yee.run(p, want_fields=True)
-    with gpu.Grid(p, prec=gpu.FP32, variant=4, kseg=32, box_seg=240) as g:
+    with gpu.Grid(p, prec=gpu.FP32, variant=4, kseg=32, box_seg=256) as g:
         assert gpu.tb_box(g.h) == (32, 735, 16, 367, 0, 241)
         g.step(64)
         g.step(64)
