@@ -111,6 +111,19 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// bulk tensor store of a staged box (shared -> global), tracked by the thread's bulk group
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// this thread's bulk stores have read their shared sources / are complete
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -255,6 +268,8 @@ struct GemmArgs {
     int ld_z;
     int qvalid;              // WGRAD: only columns < qvalid are written
     int *status;
+    int tma_store;           // inference (persistent kernel): a (HIDDEN) or y (OUT) stored by TMA through the store map
+    int out_row0;            // OUT with tma_store: row of y's first row in the store map
 };
 
 // Epilogue of 32 accumulator columns of one row: r = FP32 accumulator values of row `row`,
@@ -351,6 +366,36 @@ __device__ __forceinline__ void epi_hidden_staged(const GemmArgs &g, const uint3
     __syncwarp();
 }
 
+// The same epilogue with the 32 x 32 BF16 chunk written by a bulk tensor store: the warp fills its
+// 2 KB stage (rows of 64 bytes, 16-byte units placed by the 64-byte swizzle of the store map,
+// unit u of row r at u ^ ((r >> 1) & 3), so that a quarter-warp's row writes hit distinct banks)
+// and lane 0 issues the store.  The stage is refilled only after the previous store has read it.
+__device__ __forceinline__ void epi_hidden_tma(const CUtensorMap *tc, const uint32_t (&r)[32], int row0, int lane,
+                                               int q, const float *bias, uint8_t *stg)
+{
+    uint32_t pk[16];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 b4 = reinterpret_cast<const float4 *>(bias + q)[i];
+        const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1])),
+                                          make_float2(b4.x, b4.y)));
+        const float2 b = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])),
+                                          make_float2(b4.z, b4.w)));
+        pk[2 * i] = pack_bf16(a.x, a.y);
+        pk[2 * i + 1] = pack_bf16(b.x, b.y);
+    }
+    if (lane == 0) bulk_wait_read();
+    __syncwarp();
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<uint4 *>(stg + lane * 64 + ((j ^ sw) << 4)) =
+            make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) tma_store_2d(tc, q, row0, smem_u32(stg));
+}
+
 // Output-layer epilogue (bias, FP32 y only): the same staging, one 16-column half of the
 // chunk at a time (64 bytes of a row each)
 __device__ __forceinline__ void epi_out_staged(const GemmArgs &g, const uint32_t (&r)[32], int row0, int lane,
@@ -376,6 +421,34 @@ __device__ __forceinline__ void epi_out_staged(const GemmArgs &g, const uint32_t
             *reinterpret_cast<uint4 *>(g.out_f32 + (size_t)(row0 + rr) * g.ld_f32 + q + 16 * h + 4 * cc) = val;
         }
         __syncwarp();
+    }
+}
+
+// Output-layer epilogue through the bulk stores: each 16-column half of the chunk (64 bytes of a
+// row, FP32) goes through the warp's 2 KB stage with the same 64-byte swizzle as above.
+__device__ __forceinline__ void epi_out_tma(const CUtensorMap *tc, const uint32_t (&r)[32], int row0, int lane,
+                                           int q, const float *bias, uint8_t *stg)
+{
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 16 * h + 4 * j;
+            const float4 b4 = *reinterpret_cast<const float4 *>(bias + q + c);
+            v[j] = make_uint4(__float_as_uint(__uint_as_float(r[c]) + b4.x),
+                              __float_as_uint(__uint_as_float(r[c + 1]) + b4.y),
+                              __float_as_uint(__uint_as_float(r[c + 2]) + b4.z),
+                              __float_as_uint(__uint_as_float(r[c + 3]) + b4.w));
+        }
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(stg + lane * 64 + ((j ^ sw) << 4)) = v[j];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tma_store_2d(tc, q + 16 * h, row0, smem_u32(stg));
     }
 }
 
@@ -523,15 +596,31 @@ struct PersistSmem {
     static constexpr int NBAR = 2 * ST + 5;     // full, empty, tmem_full[2], tmem_empty[2], drain
     // bias of all Q <= 512 columns, read as float4: 16-byte (here 128-byte) aligned
     static constexpr int BIAS_OFF = (BAR_OFF + 8 * NBAR + 64 + 127) / 128 * 128;
-    // per epilogue warp: 32 rows of staged BF16 output (epi_hidden_staged)
-    static constexpr int STG_OFF = BIAS_OFF + 4 * 512;
-    static constexpr int BYTES = STG_OFF + kEpiWarps * 32 * kStageRow + 1024;
+    // per epilogue warp: its staging rows (epi_hidden_staged, epi_out_staged: 32 rows of 80 bytes;
+    // epi_hidden_tma: a 2 KB stage, 512-byte aligned for the store map's 64-byte swizzle)
+    static constexpr int STG_STRIDE = 3072;
+    static constexpr int STG_OFF = (BIAS_OFF + 4 * 512 + 1023) / 1024 * 1024;
+    static constexpr int BYTES = STG_OFF + kEpiWarps * STG_STRIDE + 1024;
+    static_assert(STG_STRIDE >= 32 * kStageRow && STG_STRIDE % 512 == 0, "staging per warp");
     static_assert(STG_OFF % 16 == 0, "16-byte staging writes");
     static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
     static_assert(BIAS_OFF % 16 == 0, "float4 reads of the staged bias");
     static constexpr uint32_t TMEM_COLS = 2 * NT;
     static_assert(2 * NT <= 512, "two accumulators must fit the 512 TMEM columns");
 };
+
+// the hidden-layer inference epilogue writes through the store map (the host sets tma_store only
+// with a map of the output buffer)
+__device__ __forceinline__ bool staged_tma_ok(const GemmArgs &g)
+{
+    return g.tma_store && g.mode == MODE_HIDDEN && g.out_bf && !g.out_f32 && !g.out_t && g.bias;
+}
+// the output-layer inference epilogue writes y through the store map; out_row0 is the first row of
+// this GEMM's y inside that map
+__device__ __forceinline__ bool out_tma_ok(const GemmArgs &g)
+{
+    return g.tma_store && g.mode == MODE_OUT && g.out_f32 && g.bias;
+}
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -540,7 +629,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 
 template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, GemmArgs g)
+k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                   const __grid_constant__ CUtensorMap tc, GemmArgs g)
 {
     using S = PersistSmem<NT>;
     constexpr int ST = S::ST;
@@ -656,7 +746,8 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
         // the layer's bias, once per CTA, for every tile's epilogue (named barrier 1: the
         // epilogue warps only)
         float *sbias = reinterpret_cast<float *>(sm + S::BIAS_OFF);
-        uint8_t *stg = sm + S::STG_OFF + (warp - 2) * 32 * kStageRow;
+        uint8_t *stg = sm + S::STG_OFF + (warp - 2) * S::STG_STRIDE;
+        const bool tstore = staged_tma_ok(g), ostore = out_tma_ok(g);
         const bool staged = g.mode == MODE_HIDDEN && g.out_bf && !g.out_f32 && !g.out_t && g.bias;
         const bool staged_out = g.mode == MODE_OUT && g.out_f32 && g.bias && (g.ld_f32 & 3) == 0;
         if (g.bias)
@@ -682,12 +773,16 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
             tmem_wait32(ra);
             for (int c0 = cb; c0 < cb + NCOL; c0 += 64) {
                 tmem_ld32_async(tl + c0 + 32, rb);
-                if (staged) epi_hidden_staged(g, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
+                if (tstore) epi_hidden_tma(&tc, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
+                else if (staged) epi_hidden_staged(g, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
+                else if (ostore) epi_out_tma(&tc, ra, g.out_row0 + p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
                 else if (staged_out) epi_out_staged(g, ra, p0 + 32 * qtr, lane, q0 + c0, sbias, stg);
                 else epi_chunk(g, ra, row, q0 + c0, sbias);
                 tmem_wait32(rb);
                 if (c0 + 64 < cb + NCOL) tmem_ld32_async(tl + c0 + 64, ra);
-                if (staged) epi_hidden_staged(g, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
+                if (tstore) epi_hidden_tma(&tc, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
+                else if (staged) epi_hidden_staged(g, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
+                else if (ostore) epi_out_tma(&tc, rb, g.out_row0 + p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
                 else if (staged_out) epi_out_staged(g, rb, p0 + 32 * qtr, lane, q0 + c0 + 32, sbias, stg);
                 else epi_chunk(g, rb, row, q0 + c0 + 32, sbias);
                 if (c0 + 64 < cb + NCOL) tmem_wait32(ra);
@@ -697,6 +792,8 @@ k_mlp_gemm_persist(const __grid_constant__ CUtensorMap ta, const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty(b));
         }
+        // the stage must outlive the bulk stores that read it
+        if ((tstore || ostore) && lane == 0) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -922,7 +1019,8 @@ struct yf_mlp {
     // query buffers
     float *qx = nullptr, *qY = nullptr, *qmean = nullptr, *qest = nullptr;
     bf16 *qa0 = nullptr, *qact[2] = {};
-    CUtensorMap mQA0, mQAct[2];
+    CUtensorMap mQA0, mQAct[2], mQActSt[2];   // mQActSt: 32 x 32 boxes for the bulk stores
+    CUtensorMap mQYSt;                        // qY of all members, 16 x 32 FP32 boxes
     int *status = nullptr, *count = nullptr;
     std::vector<void *> allocs;
 };
@@ -957,6 +1055,25 @@ yf_status map2d(CUtensorMap *m, const void *base, long rows, long cols, int box_
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding an MLP tensor map failed (%d)", (int)r);
+    return YF_OK;
+}
+
+// 2-D map for the bulk stores of the inference epilogues: boxes of 32 rows of 64 bytes (32 BF16
+// or 16 FP32 columns), 64-byte swizzle (the stage layout epi_hidden_tma and epi_out_tma write)
+yf_status map2d_store(CUtensorMap *m, const void *base, long rows, long cols,
+                      CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, int box_cols = 32)
+{
+    auto enc = encoder();
+    if (!enc) return fail(YF_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    const int esz = type == CU_TENSOR_MAP_DATA_TYPE_FLOAT32 ? 4 : 2;
+    const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t str[1] = {(cuuint64_t)cols * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, 32};   // rows of 64 bytes
+    const cuuint32_t one[2] = {1, 1};
+    CUresult r = enc(m, type, 2, const_cast<void *>(base), dim, str, box, one,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(YF_E_CUDA, "encoding an MLP store map failed (%d)", (int)r);
     return YF_OK;
 }
 
@@ -1011,13 +1128,15 @@ cudaError_t launch_gemm_t(const CUtensorMap &a, const CUtensorMap &b, const Gemm
 // Large grids (at least two tiles per SM) take 2 stages: 96 KB of shared memory and 256 TMEM
 // columns per CTA let two CTAs share an SM, so one's epilogue overlaps the other's MMAs.
 // Small grids (the training GEMMs) keep 4 stages for a deeper copy pipeline.
-cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s)
+// c: store map of the output for the hidden-layer inference epilogue (with g.tma_store), else null
+cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s,
+                        const CUtensorMap *c = nullptr)
 {
     if (g.Q % 256 == 0) {
         const long tiles = (long)(g.P / kBM) * (g.Q / 256);
         if (tiles >= 2 * sm_count()) {
             // persistent: one CTA per SM (its shared memory admits no second one)
-            k_mlp_gemm_persist<256><<<sm_count(), kThreads, PersistSmem<256>::BYTES, s>>>(a, b, g);
+            k_mlp_gemm_persist<256><<<sm_count(), kThreads, PersistSmem<256>::BYTES, s>>>(a, b, c ? *c : a, g);
             return cudaGetLastError();
         }
         return launch_gemm_t<256, 4>(a, b, g, s);
@@ -1215,8 +1334,10 @@ yf_status yf_mlp_create(int members, int train_batch, int max_query, const doubl
     for (int b = 0; b < 2; ++b) {
         TRY(dalloc(m, &m->qact[b], (size_t)NQ * kWidth));
         TRY(map2d(&m->mQAct[b], m->qact[b], NQ, kWidth, kBM));
+        TRY(map2d_store(&m->mQActSt[b], m->qact[b], NQ, kWidth));
     }
     TRY(dalloc(m, &m->qY, (size_t)members * NQ * kOut));
+    TRY(map2d_store(&m->mQYSt, m->qY, (long)members * NQ, kOut, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 16));
     TRY(dalloc(m, &m->qmean, (size_t)NQ * kOut));
     TRY(dalloc(m, &m->qest, (size_t)NQ));
     TRY(dalloc(m, &m->status, 1));
@@ -1374,11 +1495,14 @@ yf_status yf_mlp_query(yf_mlp *m, const float *x, int n, yf_mem where, float *y,
             g.bias = m->master[e] + b_off(l);
             if (last) {
                 g.out_f32 = m->qY + e * ystride; g.ld_f32 = kOut;
+                g.tma_store = 1;
+                g.out_row0 = e * m->NQ;
             } else {
                 g.out_bf = m->qact[l & 1]; g.ld_bf = kWidth;
+                g.tma_store = 1;
             }
             const CUtensorMap &a = l == 0 ? m->mQA0 : m->mQAct[(l - 1) & 1];
-            YF_CUDA_TRY(launch_gemm(a, m->mW[e], g, s));
+            YF_CUDA_TRY(launch_gemm(a, m->mW[e], g, s, last ? &m->mQYSt : &m->mQActSt[l & 1]));
         }
     }
     k_ensemble<<<(n + 7) / 8, 256, 0, s>>>(m->qY, ystride, m->E, n, m->qmean, m->qest);
