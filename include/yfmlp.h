@@ -93,7 +93,9 @@ yf_status yf_mlp_sync(yf_mlp *m, double *loss);
 /* Ensemble inference: x [n][6] raw descriptors (1 <= n <= max_query, `where`).
  * y [n][512] receives the ensemble mean; est [n] (nullable) the disagreement
  * max over members, S entries (S11, S21) and frequencies of |S_member - S_mean| (complex
- * magnitude).  Outputs live in `out_where` memory; host outputs synchronise the stream. */
+ * magnitude).  Outputs live in `out_where` memory: device outputs are written in place by the
+ * ensemble kernel (stream-ordered, no synchronisation); host outputs go through the handle's
+ * device buffers and synchronise the stream. */
 yf_status yf_mlp_query(yf_mlp *m, const float *x, int n, yf_mem where, float *y, float *est,
                        yf_mem out_where);
 

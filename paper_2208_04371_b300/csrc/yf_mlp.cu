@@ -1505,13 +1505,17 @@ yf_status yf_mlp_query(yf_mlp *m, const float *x, int n, yf_mem where, float *y,
             YF_CUDA_TRY(launch_gemm(a, m->mW[e], g, s, last ? &m->mQYSt : &m->mQActSt[l & 1]));
         }
     }
+    if (out_where == YF_DEVICE) {
+        // device outputs: the ensemble pass writes them in place (no staging copy)
+        k_ensemble<<<(n + 7) / 8, 256, 0, s>>>(m->qY, ystride, m->E, n, y, est);
+        YF_CUDA_TRY(cudaGetLastError());
+        return YF_OK;
+    }
     k_ensemble<<<(n + 7) / 8, 256, 0, s>>>(m->qY, ystride, m->E, n, m->qmean, m->qest);
     YF_CUDA_TRY(cudaGetLastError());
-    const cudaMemcpyKind k = out_where == YF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    YF_CUDA_TRY(cudaMemcpyAsync(y, m->qmean, (size_t)n * kOut * sizeof(float), k, s));
-    if (est) YF_CUDA_TRY(cudaMemcpyAsync(est, m->qest, (size_t)n * sizeof(float), k, s));
-    if (out_where == YF_HOST) return check_status(m);
-    return YF_OK;
+    YF_CUDA_TRY(cudaMemcpyAsync(y, m->qmean, (size_t)n * kOut * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (est) YF_CUDA_TRY(cudaMemcpyAsync(est, m->qest, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    return check_status(m);
 }
 
 yf_status yf_mlp_gate(yf_mlp *m, const float *est, int n, double scale, double threshold,
