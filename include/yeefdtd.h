@@ -118,9 +118,11 @@ yf_status yf_grid_dt(yf_grid *g, double *dt);
  * update is the time-centred conductor form Ca = (1-L)/(1+L), Cb = (dt/eps)/(1+L),
  * L = sigma dt / (2 eps).  More than 255 distinct non-PEC edge materials returns
  * YF_E_UNSUPPORTED, as does any mu_r != 1.  mu_r may be NULL.
- * ids with where == YF_HOST (pageable or pinned) are copied on the grid's stream into a
- * device staging buffer of nz*ny*nx bytes; the call returns after the copy and the derivation
- * have finished, so the caller may reuse its array at once.  A grid that has already stepped
+ * ids with where == YF_HOST (pageable or pinned) are copied into a device staging buffer of
+ * nz*ny*nx bytes and the classes derived on a second stream the grid keeps for this, beside
+ * work still queued on the grid's stream (the zeroing of yf_reset); the call returns after the
+ * copy and the derivation have finished, so the caller may reuse its array at once, and the
+ * grid's later work is ordered after them.  Device ids are read on the grid's stream.  A grid that has already stepped
  * (a re-solve after yf_reset) keeps that buffer until yf_grid_destroy; otherwise it is freed
  * before the call returns.  A small device scratch of the derivation (about 82 KB) is kept
  * per grid. */
@@ -302,7 +304,9 @@ yf_status yf_read_sparams_acc(yf_grid *g, int kind, double z_ref, double *S_star
 /* Start a new solve on the same grid: zero fields, CPML auxiliaries, DFT accumulators,
  * step count and error bits, and reopen the geometry (yf_set_materials and
  * yf_add_pec_sheet accept new input; sheets added before are dropped).  Boundaries,
- * PML, source, ports and captured graphs are kept.  Synchronous. */
+ * PML, source, ports and captured graphs are kept.  The call first waits for the grid's queued
+ * work; the zeroing itself is queued on the grid's stream (later work there follows it; the
+ * host does not wait for it). */
 yf_status yf_reset(yf_grid *g);
 
 /* Tracing: run n steps without graphs, bracketing every kernel launch with CUDA events

@@ -97,19 +97,21 @@ static yf_status build_coeff_tables(yf_grid *g)
     return YF_OK;
 }
 
+// the edge classes and their coefficient tables from device ids, on stream s (the grid's stream,
+// or its materials stream for host ids); returns after s has finished
 static yf_status derive_materials(yf_grid *g, const uint8_t *ids_dev, int nmat, const double *eps_r,
-                                  const double *sigma, const uint8_t *is_pec)
+                                  const double *sigma, const uint8_t *is_pec, cudaStream_t s)
 {
     yf_status st = derive_edge_classes(g->nx, g->ny, g->nz, g->px, g->plane, ids_dev, nmat, eps_r,
-                                       sigma, is_pec, g->cls, &g->mat, &g->mat_scratch, g->stream);
+                                       sigma, is_pec, g->cls, &g->mat, &g->mat_scratch, s);
     if (st != YF_OK) return st;
     st = build_coeff_tables(g);
     if (st != YF_OK) return st;
-    for (size_t s = 0; s < g->sheets.size(); s += 6) {
-        st = apply_pec_sheet(g->nx, g->ny, g->nz, g->px, g->plane, g->cls, &g->sheets[s], g->stream);
+    for (size_t q = 0; q < g->sheets.size(); q += 6) {
+        st = apply_pec_sheet(g->nx, g->ny, g->nz, g->px, g->plane, g->cls, &g->sheets[q], s);
         if (st != YF_OK) return st;
     }
-    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    YF_CUDA_TRY(cudaStreamSynchronize(s));
     g->materials_done = true;
     return YF_OK;
 }
@@ -364,7 +366,7 @@ yf_status finalize(yf_grid *g)
         YF_CUDA_TRY(cudaMemset(ids, 0, ncell));
         const double er = 1.0, sg = 0.0;
         const uint8_t pec = 0;
-        st = derive_materials(g, ids, 1, &er, &sg, &pec);
+        st = derive_materials(g, ids, 1, &er, &sg, &pec, g->stream);
         cudaFree(ids);
         if (st != YF_OK) return st;
     }
@@ -469,8 +471,7 @@ yf_status reset_state(yf_grid *g)
     }
     YF_CUDA_TRY(cudaMemsetAsync(g->ctr, 0, 2 * sizeof(long long), g->stream));
     YF_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), g->stream));
-    YF_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    g->steps_done = 0;
+    g->steps_done = 0;   // the zeroing stays queued: later work on the grid's stream follows it
     return YF_OK;
 }
 
@@ -609,6 +610,8 @@ yf_status yf_grid_destroy(yf_grid *g)
     cudaFree(g->acc64); cudaFree(g->acc32); cudaFree(g->kahan); cudaFree(g->src_table_dev);
     cudaFree(g->ids_stage);
     mat_scratch_free(&g->mat_scratch);
+    if (g->mat_ready) cudaEventDestroy(g->mat_ready);
+    if (g->mstream) cudaStreamDestroy(g->mstream);
     if (g->own_stream) cudaStreamDestroy(g->stream);
     delete g;
     return YF_OK;
@@ -640,18 +643,28 @@ yf_status yf_set_materials(yf_grid *g, const uint8_t *ids, yf_mem where, int nma
     // host ids go through a device staging buffer on the grid's stream; a grid that re-solves
     // after yf_reset keeps that buffer, one set up once (a batch instance) frees it
     const bool keep = g->started;
+    cudaStream_t ms = g->stream;
     if (where == YF_HOST) {
+        // the copy and the derivation run on the materials stream, beside whatever is queued on
+        // the grid's stream (the zeroing of yf_reset); they touch none of its buffers
+        if (!g->mstream) YF_CUDA_TRY(cudaStreamCreateWithFlags(&g->mstream, cudaStreamNonBlocking));
+        if (!g->mat_ready) YF_CUDA_TRY(cudaEventCreateWithFlags(&g->mat_ready, cudaEventDisableTiming));
+        ms = g->mstream;
         if (!g->ids_stage) YF_CUDA_TRY(cudaMalloc(&g->ids_stage, ncell));
-        YF_CUDA_TRY(cudaMemcpyAsync(g->ids_stage, ids, ncell, cudaMemcpyHostToDevice, g->stream));
+        YF_CUDA_TRY(cudaMemcpyAsync(g->ids_stage, ids, ncell, cudaMemcpyHostToDevice, ms));
         ids_dev = g->ids_stage;
     }
-    yf_status st = derive_materials(g, ids_dev, nmat, eps_r, sigma, is_pec);
+    yf_status st = derive_materials(g, ids_dev, nmat, eps_r, sigma, is_pec, ms);
     if (where == YF_HOST) {
-        cudaStreamSynchronize(g->stream);   // the copy has read the caller's ids, also on errors
+        cudaStreamSynchronize(ms);   // the copy has read the caller's ids, also on errors
+        // later work on the grid's stream sees the new classes
+        cudaError_t e = cudaEventRecord(g->mat_ready, ms);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->mat_ready, 0);
         if (!keep) {
             cudaFree(g->ids_stage);
             g->ids_stage = nullptr;
         }
+        if (st == YF_OK && e != cudaSuccess) return cuda_fail(e, "yf_set_materials: ordering the grid's stream");
     }
     return st;
 }
@@ -843,7 +856,7 @@ yf_status yf_write_fields(yf_grid *g, int comp, const void *src, yf_mem where)
         YF_CUDA_TRY(cudaMemset(ids, 0, ncell));
         const double er = 1.0, sg = 0.0;
         const uint8_t pec = 0;
-        yf_status st = derive_materials(g, ids, 1, &er, &sg, &pec);
+        yf_status st = derive_materials(g, ids, 1, &er, &sg, &pec, g->stream);
         cudaFree(ids);
         if (st != YF_OK) return st;
     }

@@ -18,6 +18,10 @@ struct yf_grid {
     size_t esz = 4;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // host ids cross and their classes are derived on mstream, beside the zeroing that
+    // yf_reset queues on `stream`; `stream` then waits for mat_ready (created on first use)
+    cudaStream_t mstream = nullptr;
+    cudaEvent_t mat_ready = nullptr;
 
     // field buffers, each ex, ey, ez, hx, hy, hz at stride npts; buf[cur] is current.
     // The fused step reads buf[cur] and writes the next buffer (buf[cur ^ 1]; variant 4
