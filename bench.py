@@ -224,9 +224,10 @@ def run_reference(args, rank, world):
 
 def batched_leg(stream, steps: int = 64, accuracy: bool = True) -> dict:
     """256 uneven microstrip instances (64-192 cells per axis, 8-cell PML, 20000 steps,
-    64 frequencies) advanced together by the batched solver, against the same instances
-    solved one at a time by the single-grid solver.  Both FP32 fields with FP64 spectra; the
-    batched results equal the single-grid ones bit for bit.  Solves/s extrapolates the timed
+    64 frequencies) advanced together by the batched solver (variant 4: two steps per pass
+    over each instance's inner box, the frames one), against the same instances solved one at
+    a time by the single-grid solver.  Both FP32 fields with FP64 spectra; each batched
+    instance equals its single-grid variant-4 run bit for bit.  Solves/s extrapolates the timed
     steps to the 20000 steps of one solve."""
     import torch
     from paper_2208_04371_b300 import workloads as W
@@ -235,7 +236,7 @@ def batched_leg(stream, steps: int = 64, accuracy: bool = True) -> dict:
     nsolve = probs[0].nsteps
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with yf.Batch(probs, prec=yf.FP32, stream=stream.cuda_stream) as b:
+    with yf.Batch(probs, prec=yf.FP32, stream=stream.cuda_stream, variant=4) as b:
         tile = b.autotune(None, reps=2)
         b.step(32)
         b.sync()
@@ -256,7 +257,7 @@ def batched_leg(stream, steps: int = 64, accuracy: bool = True) -> dict:
             e1.synchronize()
             ms_single += e0.elapsed_time(e1) / steps
     return {"workload": f"{len(probs)} uneven microstrip instances, {nsolve} steps each",
-            "cells": cells, "tile_y_kseg": list(tile),
+            "cells": cells, "variant": 4, "tile_y_kseg": list(tile),
             "ms_per_step": ms_b, "gcell_s": cells / (ms_b / 1e3) / 1e9,
             "solves_per_s": len(probs) / (ms_b * nsolve / 1e3),
             "single_instance_solves_per_s": len(probs) / (ms_single * nsolve / 1e3),
@@ -267,8 +268,9 @@ def batched_leg(stream, steps: int = 64, accuracy: bool = True) -> dict:
 def batched_accuracy(stream, probs, stride: int = 32) -> dict:
     """Measured accuracy of the batched FP32 solves: every `stride`-th instance of the sweep
     (8 of 256, seeded sizes) solved for its full step count twice by the batched solver,
-    with FP32 fields and with FP64 fields (FP64 spectra both times), and the 50-ohm S and
-    the power-mode S* compared: max |S_ij(FP32) - S_ij(FP64)| over ports and frequencies."""
+    with FP32 fields on the timed path (variant 4) and with FP64 fields (one step per pass;
+    FP64 spectra both times), and the 50-ohm S and the power-mode S* compared:
+    max |S_ij(FP32) - S_ij(FP64)| over ports and frequencies."""
     import time as _t
     from paper_2208_04371_b300 import yf
     idx = list(range(0, len(probs), stride))
@@ -277,7 +279,7 @@ def batched_accuracy(stream, probs, stride: int = 32) -> dict:
     res = {}
     t0 = _t.perf_counter()
     for prec in (yf.FP32, yf.FP64):
-        with yf.Batch(sub, prec=prec, stream=stream.cuda_stream) as b:
+        with yf.Batch(sub, prec=prec, stream=stream.cuda_stream, variant=4 if prec == yf.FP32 else 2) as b:
             b.step(nsolve)
             b.sync()
             res[prec] = [b.sparams(q) for q in range(len(sub))]

@@ -376,6 +376,13 @@ yf_status yf_batch_create(int n, const yf_instance_desc *d, double dt, yf_prec p
 yf_status yf_batch_destroy(yf_batch *b);
 /* Tile height (4, 8, 16) and z-planes per work item; defaults 8 and 16. */
 yf_status yf_batch_set_tiling(yf_batch *b, int tile_y, int kseg);
+/* Variant 4 for every instance (FP32 batches, before the first step; the default is the
+ * one-step path): each instance keeps a third field buffer, and its inner box (the same box as
+ * a single grid's variant 4, one z segment per tile column) advances two steps per pass while
+ * its CPML frame and the other instances' small grids take one; the instances' results equal
+ * their single-grid variant-4 results.  Returns YF_E_INVALID for other variants or FP64,
+ * YF_E_STATE after a step. */
+yf_status yf_batch_set_variant(yf_batch *b, int variant);
 yf_status yf_batch_step(yf_batch *b, long n);
 /* YF_E_TIMEOUT / YF_E_UNSTABLE as for single grids (any instance). */
 yf_status yf_batch_sync(yf_batch *b);

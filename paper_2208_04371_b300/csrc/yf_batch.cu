@@ -34,6 +34,19 @@ struct yf_batch {
     int *status = nullptr;            // stencil error bits of the batch
     yf::SideStream side = {};
     cudaGraphExec_t graph[2] = {};
+    // variant 4 (FP32): two time steps per pass over each instance's inner box.  Every instance
+    // keeps three field buffers; all rotate together (cur in 0..2, hpar the H-copy parity)
+    int variant = 2;
+    int hpar = 0;
+    yf::TmaPlan full4 = {}, frame4 = {};   // one-step items (6 argument sets per instance); frame4 shares args and maps
+    yf::BatchItem *box_items = nullptr;    // two-step items of every instance's box
+    int box_count = 0;
+    yf::TbArgs *tb_args = nullptr;         // [n][3] by source buffer
+    CUtensorMap *tb_maps = nullptr;        // [n][3][3]
+    void *eps3 = nullptr;                  // EpiParams<float>[n][3], by current buffer
+    cudaStream_t bstream = nullptr;        // the box kernel's stream
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraphExec_t graph4[6] = {};        // chunks by state 2 cur + hpar
 };
 
 namespace yf {
@@ -93,6 +106,108 @@ void free_device(yf_batch *b)
     cudaFree(b->eps); b->eps = nullptr;
     for (int p = 0; p < 2; ++p)
         if (b->graph[p]) { cudaGraphExecDestroy(b->graph[p]); b->graph[p] = nullptr; }
+    cudaFree(b->frame4.items);
+    b->frame4 = TmaPlan{};
+    free_plan(&b->full4);
+    cudaFree(b->box_items); b->box_items = nullptr;
+    b->box_count = 0;
+    cudaFree(b->tb_args); b->tb_args = nullptr;
+    cudaFree(b->tb_maps); b->tb_maps = nullptr;
+    cudaFree(b->eps3); b->eps3 = nullptr;
+    for (int p = 0; p < 6; ++p)
+        if (b->graph4[p]) { cudaGraphExecDestroy(b->graph4[p]); b->graph4[p] = nullptr; }
+}
+
+template <typename X>
+yf_status upload(X **dst, const std::vector<X> &v)
+{
+    YF_CUDA_TRY(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(X)));
+    if (!v.empty()) YF_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice));
+    return YF_OK;
+}
+
+yf_status upload_kinds(const std::vector<BatchItem> items[5], TmaPlan *pl)
+{
+    std::vector<BatchItem> all;
+    for (int k = 0; k < 5; ++k) {
+        pl->offset[k] = (int)all.size();
+        pl->count[k] = (int)items[k].size();
+        all.insert(all.end(), items[k].begin(), items[k].end());
+    }
+    return upload(&pl->items, all);
+}
+
+// every instance follows the batch's buffer rotation (readbacks use each grid's own state)
+void set_state(yf_batch *b, int cur, int hpar)
+{
+    b->cur = cur;
+    b->hpar = hpar;
+    for (yf_grid *g : b->g) {
+        g->cur = cur;
+        g->hpar = hpar;
+    }
+}
+
+// Variant 4 tables: per instance a third field buffer (equal to the current one: nodes no kernel
+// writes must agree in all three), maps for it, its box (one two-step segment per tile column),
+// its one-step and two-step arguments and its epilogue parameters by buffer.
+yf_status prepare4(yf_batch *b)
+{
+    const int n = (int)b->g.size();
+    std::vector<BatchItem> full[5], frame[5], two;
+    std::vector<FusedArgs<float>> fa(6 * (size_t)n);
+    std::vector<CUtensorMap> fm(12 * (size_t)n), tm(9 * (size_t)n);
+    std::vector<TbArgs> ta(3 * (size_t)n);
+    std::vector<EpiParams<float>> eps(3 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+        yf_grid *g = b->g[q];
+        if (6 * g->npts > 2147483647L)
+            return fail(YF_E_INVALID, "instance %d: variant 4 needs 6 (nz+1)(ny+1) px < 2^31", q);
+        if (!g->buf[2]) {
+            const size_t bytes = 6 * g->npts * g->esz;
+            YF_CUDA_TRY(cudaMalloc(&g->buf[2], bytes));
+            for (int r = 0; r < 3; ++r)
+                if (r != g->cur) YF_CUDA_TRY(cudaMemcpyAsync(g->buf[r], g->buf[g->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+            g->tmap_tile_y = 0;
+        }
+        g->tile_y = b->tile_y;
+        g->kseg = b->kseg;
+        yf_status st = encode_maps(g);
+        if (st != YF_OK) return st;
+        int box[6] = {0, 0, 0, 0, 0, 0};
+        const bool have = choose_box(g, box);
+        tb_items(g, q, have, box, 8, g->nz + 1, full, frame, two, 0);
+        tb_step_args(g, &fa[6 * (size_t)q], &fm[12 * (size_t)q]);
+        if (have && (st = tb_box_args(g, box, 8, &ta[3 * (size_t)q], &tm[9 * (size_t)q])) != YF_OK) return st;
+        const int c0 = g->cur;
+        for (int r = 0; r < 3; ++r) {
+            g->cur = r;
+            eps[3 * (size_t)q + r] = epi_params<float>(g);
+        }
+        g->cur = c0;
+    }
+    yf_status st;
+    if ((st = upload_kinds(full, &b->full4)) != YF_OK) return st;
+    if ((st = upload_kinds(frame, &b->frame4)) != YF_OK) return st;
+    FusedArgs<float> *fad = nullptr;
+    if ((st = upload(&fad, fa)) != YF_OK) return st;
+    b->full4.args = b->frame4.args = fad;
+    if ((st = upload(&b->full4.maps, fm)) != YF_OK) return st;
+    b->frame4.maps = b->full4.maps;
+    b->full4.stride = b->frame4.stride = 6;
+    if ((st = upload(&b->box_items, two)) != YF_OK) return st;
+    b->box_count = (int)two.size();
+    if ((st = upload(&b->tb_args, ta)) != YF_OK) return st;
+    if ((st = upload(&b->tb_maps, tm)) != YF_OK) return st;
+    EpiParams<float> *ed = nullptr;
+    if ((st = upload(&ed, eps)) != YF_OK) return st;
+    b->eps3 = ed;
+    if (!b->bstream) YF_CUDA_TRY(cudaStreamCreateWithFlags(&b->bstream, cudaStreamNonBlocking));
+    if (!b->fork) YF_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    if (!b->join) YF_CUDA_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+    YF_CUDA_TRY(tb_prepare());
+    set_state(b, b->g.empty() ? 0 : b->g[0]->cur, b->g.empty() ? 0 : b->g[0]->hpar);
+    return YF_OK;
 }
 
 template <typename T>
@@ -129,11 +244,53 @@ yf_status prepare(yf_batch *b)
         st = encode_maps(g);
         if (st != YF_OK) return st;
     }
-    yf_status st = b->prec == YF_FP32 ? build_tables<float>(b) : build_tables<double>(b);
+    yf_status st = b->variant == 4 ? prepare4(b) : b->prec == YF_FP32 ? build_tables<float>(b) : build_tables<double>(b);
     if (st != YF_OK) return st;
     YF_CUDA_TRY(side_create(&b->side));
     b->started = true;
     return YF_OK;
+}
+
+// variant 4: one step over every instance (all items), then the epilogue at the new buffer
+cudaError_t single4(yf_batch *b)
+{
+    const int r = b->cur, h = b->hpar, r1 = (r + 1) % 3;
+    cudaError_t e = launch_tma_plan<float>(b->full4, b->tile_y, 2 * r + h, b->status, b->stream, &b->side);
+    if (e != cudaSuccess) return e;
+    set_state(b, r1, h ^ 1);
+    return launch_epilogue_batch<float>((const EpiParams<float> *)b->eps3, (int)b->g.size(), r1, b->stream, 3);
+}
+
+// variant 4: two steps.  The boxes n -> n+2 on the box stream, beside the frames n -> n+1 and
+// their epilogue; once the boxes are done (their outer node layer at n+1 is in the middle
+// buffer) the frames n+1 -> n+2 and their epilogue.  The epilogues touch only source and port
+// planes, which no box reads or writes.  A pair's box kernel waits for everything queued
+// before it on the batch stream.
+cudaError_t pair4(yf_batch *b)
+{
+    const int n = (int)b->g.size();
+    const int r = b->cur, h = b->hpar, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+    const EpiParams<float> *E = (const EpiParams<float> *)b->eps3;
+    const bool box = b->box_count > 0;
+    cudaError_t e;
+    if (box) {
+        if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(b->bstream, b->fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_tb2(b->box_items, b->box_count, b->tb_args, b->tb_maps, r, b->status, b->bstream, 8)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(b->join, b->bstream)) != cudaSuccess) return e;
+    }
+    if ((e = launch_tma_plan<float>(b->frame4, b->tile_y, 2 * r + h, b->status, b->stream, &b->side)) != cudaSuccess)
+        return e;
+    if ((e = launch_epilogue_batch<float>(E, n, r1, b->stream, 3)) != cudaSuccess) return e;
+    if (box && (e = cudaStreamWaitEvent(b->stream, b->join, 0)) != cudaSuccess) return e;
+    if ((e = launch_tma_plan<float>(b->frame4, b->tile_y, 2 * r1 + (h ^ 1), b->status, b->stream, &b->side)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_epilogue_batch<float>(E, n, r2, b->stream, 3)) != cudaSuccess) return e;
+    set_state(b, r2, h);
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -152,7 +309,27 @@ cudaError_t step_t(yf_batch *b)
 
 cudaError_t step_once(yf_batch *b)
 {
+    if (b->variant == 4) return single4(b);
     return b->prec == YF_FP32 ? step_t<float>(b) : step_t<double>(b);
+}
+
+// variant 4: a chunk of pairs from state (cur, hpar); the state is restored after the capture
+// and advanced by the caller after each replay
+yf_status capture4(yf_batch *b)
+{
+    cudaGraph_t graph = nullptr;
+    const int c0 = b->cur, h0 = b->hpar, key = 2 * c0 + h0;
+    YF_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t + 1 < b->chunk && e == cudaSuccess; t += 2) e = pair4(b);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    set_state(b, c0, h0);
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "capturing batch chunk"); }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph4[key], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->graph4[key] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return YF_OK;
 }
 
 yf_status capture(yf_batch *b)
@@ -247,6 +424,9 @@ yf_status yf_batch_destroy(yf_batch *b)
     for (yf_grid *g : b->g) yf_grid_destroy(g);
     cudaFree(b->status);
     side_destroy(&b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->bstream) cudaStreamDestroy(b->bstream);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return YF_OK;
@@ -265,6 +445,21 @@ yf_status yf_batch_set_tiling(yf_batch *b, int tile_y, int kseg)
     return YF_OK;
 }
 
+yf_status yf_batch_set_variant(yf_batch *b, int variant)
+{
+    if (!b) return fail(YF_E_INVALID, "yf_batch_set_variant: NULL batch");
+    if (variant == b->variant) return YF_OK;
+    if (variant != 4) return fail(YF_E_INVALID, "yf_batch_set_variant: variant must be 4 (the default is 2)");
+    if (b->prec != YF_FP32) return fail(YF_E_INVALID, "variant 4 needs FP32 fields");
+    if (b->steps_done != 0) return fail(YF_E_STATE, "yf_batch_set_variant must precede the first step");
+    if (b->chunk % 2) return fail(YF_E_STATE, "variant 4 needs an even chunk");
+    YF_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    free_device(b);
+    b->variant = 4;
+    b->started = false;   // tables, third buffers and maps are built at the next step
+    return YF_OK;
+}
+
 yf_status yf_batch_step(yf_batch *b, long n)
 {
     if (!b || n < 0) return fail(YF_E_INVALID, "yf_batch_step: bad argument");
@@ -273,6 +468,24 @@ yf_status yf_batch_step(yf_batch *b, long n)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     YF_CUDA_TRY(cudaStreamIsCapturing(b->stream, &cs));
     long done = 0;
+    if (b->variant == 4) {
+        if (cs == cudaStreamCaptureStatusNone && n >= b->chunk)
+            for (; done + b->chunk <= n; done += b->chunk) {
+                const int key = 2 * b->cur + b->hpar;
+                if (!b->graph4[key] && (st = capture4(b)) != YF_OK) return st;
+                YF_CUDA_TRY(cudaGraphLaunch(b->graph4[key], b->stream));
+                // an even chunk of pairs: the buffers rotate by chunk mod 3, the H copy stays
+                set_state(b, (b->cur + b->chunk) % 3, b->hpar);
+            }
+        for (; done + 2 <= n; done += 2) YF_CUDA_TRY(pair4(b));
+        if (done < n) {
+            YF_CUDA_TRY(single4(b));
+            ++done;
+        }
+        b->steps_done += n;
+        for (yf_grid *g : b->g) g->steps_done += n;
+        return YF_OK;
+    }
     if (cs == cudaStreamCaptureStatusNone && n >= b->chunk) {
         if (!b->graph[b->cur]) {
             st = capture(b);

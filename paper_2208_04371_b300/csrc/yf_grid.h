@@ -125,6 +125,17 @@ void tb_unchain(yf_grid *g);   // the next pair forks after everything queued be
 cudaError_t tb_join(yf_grid *g, cudaStream_t s);
 int tb_launches_pair(const yf_grid *g);
 int tb_launches_single(const yf_grid *g);
+// the pieces of a variant-4 plan for one grid, shared with the batched two-step path
+// (yf_tb_plan.cu): the inner box (false when none fits); the work items of grid `inst`
+// (one-step over the grid, one-step outside the box, two-step box items of 32 x ty tiles and
+// seg planes); the one-step arguments and maps by slot 2 * src + hpar; the two-step arguments
+// and maps by source buffer
+bool choose_box(const yf_grid *g, int box[6]);
+void tb_items(const yf_grid *g, int inst, bool have_box, const int box[6], int ty, int seg,
+              std::vector<BatchItem> full[5], std::vector<BatchItem> frame[5], std::vector<BatchItem> &two,
+              int mixed_seg = 8);
+void tb_step_args(yf_grid *g, FusedArgs<float> fa[6], CUtensorMap fm[12]);
+yf_status tb_box_args(yf_grid *g, const int box[6], int ty, TbArgs ta[3], CUtensorMap tm[9]);
 template <typename T>
 Fields<T> fields_of(const yf_grid *g, int b);
 template <typename T>

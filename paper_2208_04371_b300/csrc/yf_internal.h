@@ -145,9 +145,10 @@ cudaError_t launch_epilogue(const EpiParams<T> &p, cudaStream_t s);
 // the soft source alone (one block; step index and counter *p.src_ctr)
 template <typename T>
 cudaError_t launch_epi_source(const EpiParams<T> &p, cudaStream_t s);
-// one block per grid; eps holds two parameter sets (buffer parity 0, 1) per grid
+// one block per grid; grid q takes eps[stride q + parity]: stride 2 holds two parameter sets
+// (buffer parity 0, 1) per grid, stride 3 one per buffer of three
 template <typename T>
-cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s);
+cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s, int stride = 2);
 template <typename T>
 cudaError_t launch_fused(const FusedArgs<T> &a, int tile_y, cudaStream_t s);
 // TMA-staged fused step (yf_tma.cu); tmF maps buffer A as [6][nz+1][ny+1][px] with box
@@ -179,6 +180,9 @@ struct TmaPlan {
     int offset[5], count[5];
     void *args;
     CUtensorMap *maps;
+    // argument sets per grid: 2 (two buffers, by parity) or 6 (three, by 2 * source + hpar);
+    // 0 reads as 2.  Grid q's set p is args[stride q + p], its maps maps[2 (stride q + p) ..]
+    int stride;
 };
 template <typename T>
 cudaError_t launch_tma_plan(const TmaPlan &pl, int tile_y, int parity, int *status, cudaStream_t s,

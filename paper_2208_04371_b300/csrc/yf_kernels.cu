@@ -366,11 +366,11 @@ __global__ void __launch_bounds__(kEpiThreads) k_epi_source(EpiParams<T> P)
 
 // Many grids: block b runs the whole epilogue of grid b (parameters of the current parity).
 template <typename T>
-__global__ void __launch_bounds__(kEpiThreads) k_epilogue_batch(const EpiParams<T> *eps, int parity)
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue_batch(const EpiParams<T> *eps, int parity, int stride)
 {
     __shared__ double red[kEpiThreads / 32];
     __shared__ double vi[kMaxPorts][2];
-    const EpiParams<T> P = eps[2 * blockIdx.x + parity];
+    const EpiParams<T> P = eps[stride * blockIdx.x + parity];
     const int tid = threadIdx.x;
     const long long n = *P.ctr;
     if (tid == 0)
@@ -464,10 +464,10 @@ cudaError_t launch_epi_source(const EpiParams<T> &p, cudaStream_t s)
 }
 
 template <typename T>
-cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s)
+cudaError_t launch_epilogue_batch(const EpiParams<T> *eps, int n, int parity, cudaStream_t s, int stride)
 {
     if (n <= 0) return cudaSuccess;
-    k_epilogue_batch<T><<<n, kEpiThreads, 0, s>>>(eps, parity);
+    k_epilogue_batch<T><<<n, kEpiThreads, 0, s>>>(eps, parity, stride);
     return cudaGetLastError();
 }
 
@@ -526,7 +526,7 @@ cudaError_t launch_energy(const T *const c[6], const uint8_t *const cls[3], cons
                                             cudaStream_t);                                  \
     template cudaError_t launch_epilogue<T>(const EpiParams<T> &, cudaStream_t);            \
     template cudaError_t launch_epi_source<T>(const EpiParams<T> &, cudaStream_t);          \
-    template cudaError_t launch_epilogue_batch<T>(const EpiParams<T> *, int, int, cudaStream_t); \
+    template cudaError_t launch_epilogue_batch<T>(const EpiParams<T> *, int, int, cudaStream_t, int); \
     template cudaError_t launch_sanitize<T>(const Fields<T> &, uint8_t *const[3], int, int, \
                                             int, int, long, cudaStream_t);                  \
     template cudaError_t launch_energy<T>(const T *const[6], const uint8_t *const[3],        \

@@ -278,8 +278,9 @@ k_yee_tb2(const BatchItem *items, const TbArgs *args, const CUtensorMap *maps, i
     constexpr int WN = S::WN, WNH = S::WNH, RHA = S::RHA, REA = S::REA, RHB = S::RHB;
     extern __shared__ __align__(128) unsigned char sm[];
     const BatchItem it = items[blockIdx.x];
-    const TbArgs P = args[phase_buf];
-    const CUtensorMap *tmE = maps + 3 * phase_buf, *tmH = tmE + 1, *tmC = tmE + 2;
+    // the item's grid: its three argument sets and nine maps (one grid: inst = 0)
+    const TbArgs P = args[3 * it.inst + phase_buf];
+    const CUtensorMap *tmE = maps + 3 * (3 * it.inst + phase_buf), *tmH = tmE + 1, *tmC = tmE + 2;
     const int tid = threadIdx.x;
     const int i0 = it.i0, j0 = it.j0, kb = it.kb, ke = it.ke;
     float2 *CT = reinterpret_cast<float2 *>(sm + S::CT_OFF);

@@ -39,6 +39,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
 // are left out (the port epilogue reads and the source writes the frame's fields between
 // the two steps).  x: the longest run of admissible 32-node tile columns; y: rows aligned to
 // the frame's tile height; z: every admissible plane.  Returns false when no box fits.
+}  // namespace
+
 bool choose_box(const yf_grid *g, int box[6])
 {
     const int n = g->pml_n;
@@ -69,6 +71,8 @@ bool choose_box(const yf_grid *g, int box[6])
     box[5] = bz1;
     return true;
 }
+
+namespace {
 
 yf_status upload_items(const std::vector<BatchItem> items[5], TmaPlan *pl)
 {
@@ -119,6 +123,94 @@ void tb_free(yf_grid *g)
     g->tb = nullptr;
 }
 
+// The work items of grid `inst`, appended: the one-step items over the whole grid (full; the
+// all-CPML kind in segments of at most mixed_seg planes, 0: whole), those outside the box
+// (frame: items that straddle it in z keep their parts below and above it), and the two-step
+// box items (tiles of 32 x ty over z segments of seg planes).
+void tb_items(const yf_grid *g, int inst, bool have_box, const int B[6], int ty, int seg,
+              std::vector<BatchItem> full[5], std::vector<BatchItem> frame[5], std::vector<BatchItem> &two,
+              int mixed_seg)
+{
+    std::vector<BatchItem> own[5];   // this grid's items only: the vectors may hold other grids'
+    tma_items(inst, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, own, mixed_seg);
+    for (int k = 0; k < 5; ++k) full[k].insert(full[k].end(), own[k].begin(), own[k].end());
+    for (int k = 0; k < 5; ++k)
+        for (const BatchItem &it : own[k]) {
+            const bool inxy = have_box && it.i0 >= B[0] && it.i0 <= B[1] && it.j0 >= B[2] && it.j0 <= B[3];
+            if (!inxy || it.ke < B[4] || it.kb > B[5]) {
+                frame[k].push_back(it);
+                continue;
+            }
+            if (it.kb < B[4]) frame[k].push_back(BatchItem{inst, it.i0, it.j0, it.kb, B[4] - 1});
+            if (it.ke > B[5]) frame[k].push_back(BatchItem{inst, it.i0, it.j0, B[5] + 1, it.ke});
+        }
+    if (have_box)
+        for (int kb = B[4]; kb <= B[5]; kb += seg)
+            for (int j0 = B[2]; j0 <= B[3]; j0 += ty)
+                for (int i0 = B[0]; i0 <= B[1]; i0 += kTbTileX)
+                    two.push_back(BatchItem{inst, i0, j0, kb, std::min(B[5], kb + seg - 1)});
+}
+
+// The one-step arguments and maps of a grid with three buffers, by slot 2 * src + hpar (the
+// step reads buffer src and writes the next one)
+void tb_step_args(yf_grid *g, FusedArgs<float> fa[6], CUtensorMap fm[12])
+{
+    const int c0 = g->cur, h0 = g->hpar;
+    for (int r = 0; r < 3; ++r)
+        for (int h = 0; h < 2; ++h) {
+            g->cur = r;
+            g->hpar = h;
+            fa[2 * r + h] = fused_args<float>(g);
+            fm[2 * (2 * r + h)] = g->tmF[r];
+            fm[2 * (2 * r + h) + 1] = g->tmC;
+        }
+    g->cur = c0;
+    g->hpar = h0;
+}
+
+// The two-step arguments and maps of a grid by source buffer r (B = buffer r+1, C = r+2): the
+// E window map, the H window map and the class-tile map of each
+yf_status tb_box_args(yf_grid *g, const int B[6], int ty, TbArgs ta[3], CUtensorMap tm[9])
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
+    if (!encode) return fail(YF_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
+    const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
+    const cuuint32_t wbox[4] = {kTbWinX, (cuuint32_t)ty + 4, 1, 3};
+    const cuuint32_t hbox[4] = {kTbWinX, (cuuint32_t)ty + 3, 1, 3};
+    const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
+    const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
+    const cuuint32_t cbox[4] = {kTbClsX, (cuuint32_t)ty + 2, 1, 3};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    for (int r = 0; r < 3; ++r) {
+        TbArgs &a = ta[r];
+        a.px = g->px;
+        a.plane = g->plane;
+        a.npts = g->npts;
+        a.rdx = (float)(1.0 / g->dx);
+        a.rdy = (float)(1.0 / g->dy);
+        a.rdz = (float)(1.0 / g->dz);
+        a.db = (float)(g->dt / kMu0);
+        a.ctab = (const float *)g->ctab;
+        a.B = (float *)g->buf[(r + 1) % 3];
+        a.C = (float *)g->buf[(r + 2) % 3];
+        a.bx0 = B[0]; a.bx1 = B[1]; a.by0 = B[2]; a.by1 = B[3]; a.bz0 = B[4]; a.bz1 = B[5];
+        CUresult cr = encode(&tm[3 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr == CUDA_SUCCESS)
+            cr = encode(&tm[3 * r + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, hbox, one,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr == CUDA_SUCCESS)
+            cr = encode(&tm[3 * r + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return fail(YF_E_CUDA, "variant 4: tensor map encoding failed (%d)", (int)cr);
+    }
+    return YF_OK;
+}
+
 // Plan of variant 4 on a finalised FP32 grid whose three field buffers exist and whose field
 // maps (tmF[0..2], tmC) are encoded for the grid's tile height.
 yf_status tb_build(yf_grid *g)
@@ -136,29 +228,13 @@ yf_status tb_build(yf_grid *g)
     auto bail = [&](yf_status st) { tb_free(g); return st; };
 
     std::vector<BatchItem> full[5], frame[5], two;
-    tma_items(0, g->nx, g->ny, g->nz, g->kseg, g->tile_y, g->pml_n, g->pml_lo, g->pml_hi, full, 8);
     t->ty = g->box_ty;
     const bool have_box = choose_box(g, t->box);
     const int *B = t->box;
-    for (int k = 0; k < 5; ++k)
-        for (const BatchItem &it : full[k]) {
-            const bool inxy = have_box && it.i0 >= B[0] && it.i0 <= B[1] && it.j0 >= B[2] && it.j0 <= B[3];
-            if (!inxy || it.ke < B[4] || it.kb > B[5]) {
-                frame[k].push_back(it);
-                continue;
-            }
-            if (it.kb < B[4]) frame[k].push_back(BatchItem{0, it.i0, it.j0, it.kb, B[4] - 1});
-            if (it.ke > B[5]) frame[k].push_back(BatchItem{0, it.i0, it.j0, B[5] + 1, it.ke});
-        }
     // z-planes per two-step block: as set by yf_set_box_shape, else twice the one-step
     // segment (the two-step block re-reads four halo planes instead of two); its rings are
     // indexed modulo their depth, so any length works
-    const int seg = g->box_seg > 0 ? g->box_seg : 2 * g->kseg;
-    if (have_box)
-        for (int kb = B[4]; kb <= B[5]; kb += seg)
-            for (int j0 = B[2]; j0 <= B[3]; j0 += t->ty)
-                for (int i0 = B[0]; i0 <= B[1]; i0 += kTbTileX)
-                    two.push_back(BatchItem{0, i0, j0, kb, std::min(B[5], kb + seg - 1)});
+    tb_items(g, 0, have_box, B, t->ty, g->box_seg > 0 ? g->box_seg : 2 * g->kseg, full, frame, two);
     yf_status st;
     if ((st = upload_items(full, &t->full)) != YF_OK) return bail(st);
     if ((st = upload_items(frame, &t->frame)) != YF_OK) return bail(st);
@@ -168,66 +244,21 @@ yf_status tb_build(yf_grid *g)
                                     cudaMemcpyHostToDevice) != cudaSuccess))
         return bail(fail(YF_E_OOM, "variant 4: work items"));
 
-    // single-step arguments by slot 2 * src + hpar (B = the next buffer), shared by both plans
     std::vector<FusedArgs<float>> fa(6);
     std::vector<CUtensorMap> fm(12);
-    const int c0 = g->cur, h0 = g->hpar;
-    for (int r = 0; r < 3; ++r)
-        for (int h = 0; h < 2; ++h) {
-            g->cur = r;
-            g->hpar = h;
-            fa[2 * r + h] = fused_args<float>(g);
-            fm[2 * (2 * r + h)] = g->tmF[r];
-            fm[2 * (2 * r + h) + 1] = g->tmC;
-        }
-    g->cur = c0;
-    g->hpar = h0;
+    tb_step_args(g, fa.data(), fm.data());
     if (cudaMalloc(&t->full.args, fa.size() * sizeof(FusedArgs<float>)) != cudaSuccess ||
         cudaMemcpy(t->full.args, fa.data(), fa.size() * sizeof(FusedArgs<float>), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMalloc(&t->full.maps, fm.size() * sizeof(CUtensorMap)) != cudaSuccess ||
         cudaMemcpy(t->full.maps, fm.data(), fm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(YF_E_OOM, "variant 4: step arguments"));
+    t->full.stride = t->frame.stride = 6;
     t->frame.args = t->full.args;
     t->frame.maps = t->full.maps;
 
-    // two-step arguments and maps by source buffer r: B = buf[r+1], C = buf[r+2]
     TbArgs ta[3];
     CUtensorMap tm[9];
-    const cuuint64_t gdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 6};
-    const cuuint64_t gstr[3] = {(cuuint64_t)g->px * 4, (cuuint64_t)g->plane * 4, (cuuint64_t)g->npts * 4};
-    const cuuint32_t wbox[4] = {kTbWinX, (cuuint32_t)t->ty + 4, 1, 3};
-    const cuuint32_t hbox[4] = {kTbWinX, (cuuint32_t)t->ty + 3, 1, 3};
-    const cuuint64_t cdim[4] = {(cuuint64_t)g->px, (cuuint64_t)(g->ny + 1), (cuuint64_t)(g->nz + 1), 3};
-    const cuuint64_t cstr[3] = {(cuuint64_t)g->px, (cuuint64_t)g->plane, (cuuint64_t)g->npts};
-    const cuuint32_t cbox[4] = {kTbClsX, (cuuint32_t)t->ty + 2, 1, 3};
-    const cuuint32_t one[4] = {1, 1, 1, 1};
-    for (int r = 0; r < 3; ++r) {
-        TbArgs &a = ta[r];
-        a.px = g->px;
-        a.plane = g->plane;
-        a.npts = g->npts;
-        a.rdx = (float)(1.0 / g->dx);
-        a.rdy = (float)(1.0 / g->dy);
-        a.rdz = (float)(1.0 / g->dz);
-        a.db = (float)(g->dt / kMu0);
-        a.ctab = (const float *)g->ctab;
-        a.B = (float *)g->buf[(r + 1) % 3];
-        a.C = (float *)g->buf[(r + 2) % 3];
-        a.bx0 = B[0]; a.bx1 = B[1]; a.by0 = B[2]; a.by1 = B[3]; a.bz0 = B[4]; a.bz1 = B[5];
-        // per source buffer: the E window map, the H window map, the class-tile map
-        CUresult cr = encode(&tm[3 * r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, wbox, one,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr == CUDA_SUCCESS)
-            cr = encode(&tm[3 * r + 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->buf[r], gdim, gstr, hbox, one,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr == CUDA_SUCCESS)
-            cr = encode(&tm[3 * r + 2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, g->cls_base, cdim, cstr, cbox, one,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr != CUDA_SUCCESS) return bail(fail(YF_E_CUDA, "variant 4: tensor map encoding failed (%d)", (int)cr));
-    }
+    if ((st = tb_box_args(g, B, t->ty, ta, tm)) != YF_OK) return bail(st);
     if (cudaMalloc(&t->args, sizeof(ta)) != cudaSuccess ||
         cudaMemcpy(t->args, ta, sizeof(ta), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMalloc(&t->maps, sizeof(tm)) != cudaSuccess ||

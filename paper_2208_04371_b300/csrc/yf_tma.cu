@@ -512,7 +512,7 @@ __device__ __forceinline__ void tma_tile(const FusedArgs<T> &P, const CUtensorMa
 template <typename T, int TX, int TYT, int CY, int PM>
 __global__ void __launch_bounds__(TX *TYT, (sizeof(T) == 4 && CY == 1) ? ((PM == 7) ? 4 : 5) : 1)
     k_yee_tma_batch(const BatchItem *items, const FusedArgs<T> *args, const CUtensorMap *maps,
-                    int parity, int *status)
+                    int parity, int stride, int *status)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     using Lay = TmaLayout<T, TX, TYT * CY>;
@@ -520,11 +520,11 @@ __global__ void __launch_bounds__(TX *TYT, (sizeof(T) == 4 && CY == 1) ? ((PM ==
     const BatchItem it = items[blockIdx.x];
     FusedArgs<T> *sP = reinterpret_cast<FusedArgs<T> *>(sm + Lay::BYTES);
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const int *src = reinterpret_cast<const int *>(args + 2 * it.inst + parity);
+    const int *src = reinterpret_cast<const int *>(args + stride * it.inst + parity);
     int *dst = reinterpret_cast<int *>(sP);
     for (int q = tid; q < (int)(sizeof(FusedArgs<T>) / 4); q += TX * TYT) dst[q] = src[q];
     __syncthreads();
-    const CUtensorMap *m = maps + 2 * (2 * it.inst + parity);
+    const CUtensorMap *m = maps + 2 * (stride * it.inst + parity);
     tma_tile<T, TX, TYT, CY, PM>(*sP, m, m + 1, status, sm, it.i0, it.j0, it.kb, it.ke);
 }
 
@@ -559,7 +559,8 @@ cudaError_t launch_kind(const TmaPlan &pl, int kind, int parity, int *status, cu
     const int cnt = pl.count[kind];
     if (cnt <= 0) return cudaSuccess;
     k_yee_tma_batch<T, TX, TYT, CY, PM><<<cnt, dim3(TX, TYT), batch_bytes<T, TX, TYT, CY, PM>(), s>>>(
-        pl.items + pl.offset[kind], (const FusedArgs<T> *)pl.args, pl.maps, parity, status);
+        pl.items + pl.offset[kind], (const FusedArgs<T> *)pl.args, pl.maps, parity, pl.stride > 0 ? pl.stride : 2,
+        status);
     return cudaGetLastError();
 }
 

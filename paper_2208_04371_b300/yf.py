@@ -116,6 +116,7 @@ _SIGS = {
     "yf_batch_create": (_i, [_i, C.POINTER(InstanceDesc), _d, _i, _vp, C.POINTER(_vp)]),
     "yf_batch_destroy": (_i, [_vp]),
     "yf_batch_set_tiling": (_i, [_vp, _i, _i]),
+    "yf_batch_set_variant": (_i, [_vp, _i]),
     "yf_batch_step": (_i, [_vp, C.c_long]),
     "yf_batch_sync": (_i, [_vp]),
     "yf_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_long), _dp, C.POINTER(C.c_long)]),
@@ -540,7 +541,7 @@ class Batch:
     """Owns a yf_batch of workloads.Problem instances (one shared time step)."""
 
     def __init__(self, probs, prec=FP32, stream=None, dt: float = 0.0, tile_y: int = 8,
-                 kseg: int = 16):
+                 kseg: int = 16, variant: int = 2):
         self.probs = list(probs)
         if dt <= 0.0:
             # the instances' own Courant numbers: the smallest of their time steps
@@ -590,6 +591,8 @@ class Batch:
         self.h = h.value
         if (tile_y, kseg) != (8, 16):
             _check(_lib.yf_batch_set_tiling(C.c_void_p(self.h), tile_y, kseg))
+        if variant != 2:
+            _check(_lib.yf_batch_set_variant(C.c_void_p(self.h), variant))
         self._keep.append(descs)
         cells = C.c_long()
         dtv = C.c_double()
@@ -598,6 +601,9 @@ class Batch:
 
     def set_tiling(self, tile_y, kseg):
         _check(_lib.yf_batch_set_tiling(C.c_void_p(self.h), tile_y, kseg))
+
+    def set_variant(self, variant):
+        _check(_lib.yf_batch_set_variant(C.c_void_p(self.h), variant))
 
     def autotune(self, cache_path=None, reps=3):
         ty, ks = C.c_int(), C.c_int()

@@ -109,3 +109,48 @@ def test_batch_takes_the_instances_courant_number(gpu):
         Vb, Ib = b.port_dfts(0)
         Vg, Ig = g.port_dfts()
     assert np.array_equal(Vb, Vg) and np.array_equal(Ib, Ig)
+
+
+BOX_DIMS = [(120, 60, 40), (96, 48, 36), (150, 70, 44), (56, 40, 36), (100, 50, 30)]
+
+
+@pytest.mark.parametrize("tile_y,kseg", [(8, 16), (4, 7)])
+def test_two_step_batch_equals_single_grids_bitwise(gpu, tile_y, kseg):
+    """Variant 4 for a batch: instances with inner boxes of one to three tile columns, one too
+    small for a box and one closed by PEC walls; 151 steps (graph chunks of pairs, direct
+    pairs and one single step).  Every instance equals its single-grid variant-4 run bit for bit,
+    fields and port spectra."""
+    rng = W.SplitMix64(0xB0C5)
+    probs = [W.batch_instance(rng, nsteps=151, nfreq=16, dims=d) for d in BOX_DIMS]
+    probs[4].bc = (0, 0, 0, 0, 0, 0)
+    n = 151
+    boxes = []
+    with gpu.Batch(probs, prec=gpu.FP32, tile_y=tile_y, kseg=kseg, variant=4) as b:
+        b.step(n)
+        b.sync()
+        got = [b.fields(q) for q in range(len(probs))]
+        dft = [b.port_dfts(q) for q in range(len(probs))]
+        dt = b.dt
+    for q, p in enumerate(probs):
+        with gpu.Grid(p, prec=gpu.FP32, dt=dt, variant=4, tile_y=tile_y, kseg=kseg) as g:
+            boxes.append(gpu.tb_box(g.h))
+            g.step(n)
+            g.sync()
+            assert np.array_equal(got[q], g.fields()), q
+            V, I = g.port_dfts()
+            assert np.array_equal(dft[q][0], V) and np.array_equal(dft[q][1], I), q
+    assert sum(bx is not None for bx in boxes) >= 3 and boxes[3] is None, boxes
+
+
+def test_two_step_batch_is_refused_for_fp64_and_after_a_step(gpu):
+    rng = W.SplitMix64(0xB0C6)
+    probs = [W.batch_instance(rng, nsteps=10, nfreq=8, dims=(96, 48, 36))]
+    with gpu.Batch(probs, prec=gpu.FP64) as b:
+        with pytest.raises(gpu.YFError):
+            b.set_variant(4)
+    with gpu.Batch(probs, prec=gpu.FP32) as b:
+        b.step(2)
+        with pytest.raises(gpu.YFError):
+            b.set_variant(4)
+        with pytest.raises(gpu.YFError):
+            b.set_variant(3)
