@@ -265,6 +265,27 @@ def batched_leg(stream, steps: int = 64, accuracy: bool = True) -> dict:
             "accuracy": batched_accuracy(stream, probs) if accuracy else None}
 
 
+def batched_steps(stream, variant: int, steps: int) -> dict:
+    """The batched sweep's stepping alone (for launch lists): the 256 instances at tiling 8 x 32,
+    two untimed steps, then `steps` timed steps."""
+    import torch
+    from paper_2208_04371_b300 import workloads as W
+    from paper_2208_04371_b300 import yf
+    probs = W.config_batched()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with yf.Batch(probs, prec=yf.FP32, stream=stream.cuda_stream, tile_y=8, kseg=32, variant=variant) as b:
+        b.step(2)
+        b.sync()
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1) / max(1, steps)
+        return {"variant": variant, "steps": steps, "ms_per_step": ms, "gcell_s": b.cells / (ms / 1e3) / 1e9}
+
+
 def batched_accuracy(stream, probs, stride: int = 32) -> dict:
     """Measured accuracy of the batched FP32 solves: every `stride`-th instance of the sweep
     (8 of 256, seeded sizes) solved for its full step count twice by the batched solver,
@@ -540,6 +561,10 @@ def main():
                     help="skip the batched leg's FP32-vs-FP64 accuracy solves")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="only the surrogate inference leg (profiling captures)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched sweep's stepping, tiling 8 x 32, --steps steps after 2 (profiling captures)")
+    ap.add_argument("--batch-variant", type=int, default=4, choices=[2, 4],
+                    help="with --batched-only: 4 two steps per pass over each instance's box, 2 one step")
     ap.add_argument("--nz", type=int, default=256,
                     help="planes of the lossy line (profiling captures only; the bench line is nz=256)")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
@@ -560,6 +585,12 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"surrogate": surrogate_leg(torch.cuda.Stream())}), flush=True)
+        return
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"batched_steps": batched_steps(torch.cuda.Stream(), args.batch_variant, args.steps)}),
+              flush=True)
         return
     if world > 1:
         import torch
