@@ -183,6 +183,98 @@ def cpu_oracle_sample(target_s: float = 5.0, samples: int = 3):
         s.close()
 
 
+def oracle_mlp_rate() -> float:
+    """Queries/s of the FP64 MLP oracle's forward (numpy) for the 4-member ensemble on 1024
+    queries of the surrogate's input distribution, best of two (the first warms the BLAS)."""
+    import time as _t
+    from oracle import mlp as omlp
+    from paper_2208_04371_b300 import workloads as W
+    from paper_2208_04371_b300 import yf
+    params = [yf.mlp_unflatten(W.mlp_init(0x5EED + 7919 * e)) for e in range(4)]
+    xs = W.surrogate_inputs(W.SplitMix64(0x51), 1024)
+    lo, hi = np.array(W.SURROGATE_LO), np.array(W.SURROGATE_HI)
+    xm = (xs - lo) * (2.0 / (hi - lo)) - 1.0
+    best = 0.0
+    for _ in range(2):
+        t0 = _t.perf_counter()
+        for prm in params:
+            omlp.forward(prm, xm)
+        best = max(best, 1024 / (_t.perf_counter() - t0))
+    return best
+
+
+def cpu_baseline_table() -> dict:
+    """The cpu_baseline leg for every workload (the bench line carries the lossy line's): the
+    FP64 oracle on the host's cores and on one thread, each beside the GPU figure it sets off.
+    C1 the 64x32x24 FP64 microstrip in full (2000 steps); C3 every 32nd instance of the
+    batched sweep (8 of 256), stepping alone timed and extrapolated to solves/s per cell update;
+    C4 the 256x128x128 long-run line on a bounded subrun; C5 the FP64 MLP forward of the
+    4-member ensemble on 1024 queries (numpy, its BLAS on all threads, then one).  GPU figures:
+    C1 and C4 timed here through the library; C3 and C5 are the bench line's batched and
+    surrogate legs."""
+    import subprocess
+    import sys
+    import torch
+    from oracle import yee
+    from paper_2208_04371_b300 import workloads as W
+    from paper_2208_04371_b300 import yf
+    threads = os.cpu_count() or 1
+
+    def oracle_rate(probs, nsteps, nsteps1):
+        cells = sec = cells1 = sec1 = 0.0
+        for p in probs:
+            with yee.Stepper(p, threads=threads) as st:
+                st.advance(1)                       # first touch of the arrays
+                sec += st.advance(nsteps, threads=threads)
+                sec1 += st.advance(nsteps1, threads=1)
+            cells += p.cells * nsteps
+            cells1 += p.cells * nsteps1
+        return cells / sec / 1e9, cells1 / sec1 / 1e9, sec + sec1
+
+    def gpu_rate(p, prec, nsteps):
+        s = torch.cuda.Stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with yf.Grid(p, prec=prec, stream=s.cuda_stream) as g:
+            g.step(64)
+            g.sync()
+            e0.record(s)
+            g.step(nsteps)
+            e1.record(s)
+            e1.synchronize()
+            g.sync()
+        return p.cells * nsteps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    out = {"threads": threads, "kind": "oracle"}
+    p1 = W.config_small_fp64()
+    a, one, sec = oracle_rate([p1], p1.nsteps, p1.nsteps)
+    out["C1 FP64 microstrip 64x32x24, 2000 steps"] = {
+        "oracle_gcell_s": a, "oracle_single_thread_gcell_s": one, "oracle_seconds": sec,
+        "gpu_gcell_s": gpu_rate(p1, yf.FP64, p1.nsteps)}
+    probs = W.config_batched()
+    sub = probs[::32]
+    a, one, sec = oracle_rate(sub, 40, 4)
+    mean_cells = float(np.mean([p.cells for p in probs]))
+    out["C3 batched sweep, 8 of 256 instances sampled"] = {
+        "oracle_gcell_s": a, "oracle_single_thread_gcell_s": one, "oracle_seconds": sec,
+        "oracle_solves_per_s": a * 1e9 / (mean_cells * probs[0].nsteps),
+        "steps_sampled": 40, "gpu": "the bench line's batched leg"}
+    p4 = W.config_long_run(nsteps=0)
+    a, one, sec = oracle_rate([p4], 200, 20)
+    out["C4 long-run line 256x128x128, 200-step subrun"] = {
+        "oracle_gcell_s": a, "oracle_single_thread_gcell_s": one, "oracle_seconds": sec,
+        "gpu_gcell_s": gpu_rate(p4, yf.FP32, 2000)}
+    qa = oracle_mlp_rate()
+    # one BLAS thread: the same forward in a child process started with one thread
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-mlp-rate"], env=env,
+                       capture_output=True, text=True, check=True)
+    q1 = float(r.stdout.strip().splitlines()[-1])
+    out["C5 surrogate ensemble, 1024 queries"] = {
+        "oracle_queries_per_s": qa, "oracle_single_thread_queries_per_s": q1,
+        "gpu": "the bench line's surrogate leg"}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle arm: rank 0 times the FP64 CPU oracle; other ranks exit without work.
     One bench step is one bounded sample of oracle steps on the same line, so that the whole
@@ -561,6 +653,9 @@ def main():
                     help="skip the batched leg's FP32-vs-FP64 accuracy solves")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="only the surrogate inference leg (profiling captures)")
+    ap.add_argument("--oracle-mlp-rate", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="only the cpu_baseline leg for every workload (FP64 oracle beside the GPU figures)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched sweep's stepping, tiling 8 x 32, --steps steps after 2 (profiling captures)")
     ap.add_argument("--batch-variant", type=int, default=4, choices=[2, 4],
@@ -585,6 +680,14 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"surrogate": surrogate_leg(torch.cuda.Stream())}), flush=True)
+        return
+    if args.oracle_mlp_rate:
+        print(oracle_mlp_rate(), flush=True)
+        return
+    if args.cpu_table:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"cpu_baseline_table": cpu_baseline_table()}), flush=True)
         return
     if args.batched_only:
         import torch
