@@ -154,3 +154,25 @@ def test_two_step_batch_is_refused_for_fp64_and_after_a_step(gpu):
             b.set_variant(4)
         with pytest.raises(gpu.YFError):
             b.set_variant(3)
+
+
+def test_two_step_batch_after_autotune_equals_single_grids(gpu, tmp_path):
+    """The benchmark's order: a variant-4 batch autotuned (its tables rebuilt per tiling, every
+    instance reset afterwards), then stepped; each instance still equals its single-grid
+    variant-4 run bit for bit at the tiling the tuner chose."""
+    rng = W.SplitMix64(0xB0C7)
+    probs = [W.batch_instance(rng, nsteps=64, nfreq=8, dims=d) for d in BOX_DIMS[:3]]
+    n = 64
+    with gpu.Batch(probs, prec=gpu.FP32, variant=4) as b:
+        ty, ks = b.autotune(str(tmp_path / "tiles.json"), reps=1)
+        for q in range(len(probs)):
+            assert not np.any(b.fields(q)), "tuning must leave the fields at zero"
+        b.step(n)
+        b.sync()
+        got = [b.fields(q) for q in range(len(probs))]
+        dt = b.dt
+    for q, p in enumerate(probs):
+        with gpu.Grid(p, prec=gpu.FP32, dt=dt, variant=4, tile_y=ty, kseg=ks) as g:
+            g.step(n)
+            g.sync()
+            assert np.array_equal(got[q], g.fields()), q
