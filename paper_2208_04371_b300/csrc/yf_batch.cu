@@ -8,6 +8,13 @@
 // port epilogue.  A work item is one 32 x tile_y node column of one instance over a
 // z-segment; per-instance kernel arguments and tensor maps live in device memory, two sets
 // each (field-buffer parity 0 and 1).  Chunks of steps replay from captured CUDA graphs.
+//
+// With variant 4 (FP32), every instance with an inner box (the single-grid variant-4 box) has
+// it advanced two steps per pass: a pair of steps is one box-kernel launch over every
+// instance's box items, beside the one-step frame kinds of the first step and their epilogue,
+// then the frame kinds of the second step and theirs.  Instances then keep three field
+// buffers; arguments and maps come in six one-step sets (2 * source buffer + H-copy parity),
+// three two-step sets and three epilogue sets per instance.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
